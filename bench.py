@@ -1,0 +1,498 @@
+"""Benchmark: cubic B-spline interpolation (BSI) of FFD control grids on GB300.
+
+One step = one pass of the whole hot path over one CT-shaped volume
+(512 x 512 x 300 voxels, control spacing 5 x 5 x 5, smooth Gaussian random
+control displacements): the forward field (Eq. 1) and the adjoint gather of a
+voxel gradient back onto the control grid -- what every iteration of the FFD
+registration loop computes.  ``value`` is voxels per second of that step,
+summed over ranks (independent volumes per rank: weak scaling, no collective
+on the data path).
+
+Reported alongside (same run): forward-only FP32 and BF16, the adjoint alone,
+the 512^3 spacing sweep, the 64-volume uneven batch (forward + adjoint, one
+CUDA-graph replay per step), the end-to-end rate through the public API with
+host buffers, the roofline of the dominant kernel against the measured HBM
+peak, GPU clocks sampled during the timed region, and the FP64 CPU oracle
+timed on the host cores on a bounded slab of the same workload.
+
+``--impl reference`` times the FP64 oracle (the only reference this method
+has: the paper ships no code) on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import pathlib
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = pathlib.Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "deformation-field Gvoxels/s (fwd, fwd+adjoint, batched) and % HBM roofline"
+UNIT = "Gvoxels/s"
+CT_SHAPE, CT_SPACING = (300, 512, 512), (5, 5, 5)
+WORKLOAD = ("CT-shaped 512x512x300 voxels, spacing 5x5x5, FP32 control grid 106x106x63x3 "
+            "(smooth Gaussian random field, std 3 voxels), forward + adjoint per step")
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true", help="main step only (profiling runs)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle leg")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, ws, device=None):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples in the background (200 ms period)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [v.strip() for v in line.split(",")]))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self, t0, t1):
+        rows = [s for (t, s) in self.samples if t0 <= t <= t1 and len(s) >= 9]
+        window = "timed region"
+        if not rows:  # short timed region: fall back to the whole sampled span
+            rows = [s for (_, s) in self.samples if len(s) >= 9]
+            window = "whole run (timed region shorter than one sample)"
+        if not rows:
+            return None
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "window": window,
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    for name in ("bsi_kernels.cuh", "bsi_forward.cu", "bsi_adjoint.cu", "bsi_geometry.h", "bsi_weights.cuh"):
+        h.update((ROOT / "paper_2004_05962_gb300" / "csrc" / name).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    p = ROOT / "profiles" / "dram_traffic.md"
+    if not p.exists():
+        return None
+    sha = kernel_sources_sha()
+    for line in p.read_text().splitlines():
+        m = re.match(r"\|\s*(\S+)\s*\|\s*(\S+)\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9a-f]+)\s*\|", line)
+        if m and m.group(1) == kernel and m.group(4) == sha:
+            return float(m.group(3))
+    return None
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2004_05962_gb300 import build as pbuild
+
+    pbuild.build()
+    import paper_2004_05962_gb300 as P
+    from paper_2004_05962_gb300 import model, synth
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    s = torch.cuda.current_stream(dev)
+    shape, spacing = CT_SHAPE, CT_SPACING
+    nvox = int(np.prod(shape))
+
+    phi = torch.from_numpy(synth.gaussian_random_phi(shape, spacing, 3.0, 2.0, seed=2 + rank)).to(dev)
+    grad = torch.from_numpy(synth.normal_field(shape, seed=4 + rank)).to(dev)
+    field = torch.empty(shape + (3,), device=dev)
+    dphi = torch.empty_like(phi)
+    wsb = P.bsi_adjoint_workspace_bytes(shape, spacing)
+    work = torch.empty(wsb, dtype=torch.uint8, device=dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(s)
+        P.bsi_field_forward(phi, shape, spacing, out=field)
+        if ev is not None:
+            ev[1].record(s)
+        P.bsi_field_adjoint(grad, spacing, out=dphi, workspace=work)
+        if ev is not None:
+            ev[2].record(s)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for k in range(args.steps):
+        step(evs[k])
+    e1.record(s)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t1 = time.time()
+    clk.stop()
+    ms_total = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+    ms_step = ms_total / args.steps
+    fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    adj_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    value = ws * nvox / (ms_step * 1e-3) / 1e9
+    launches = 3 * args.steps  # forward, adjoint partials, adjoint reduce per step
+
+    hbm_peak, peak_kind = measured_peaks()
+    fwd_bytes = model.forward_bytes(shape, spacing)
+    adj_bytes = model.adjoint_bytes(shape, spacing)
+    fwd_gbs = fwd_bytes / (fwd_ms * 1e-3) / 1e9
+    adj_gbs = adj_bytes / (adj_ms * 1e-3) / 1e9
+    dominant = "bsi_forward_kernel" if fwd_ms >= adj_ms else "bsi_field_adjoint (partials + reduce)"
+    if fwd_ms >= adj_ms:
+        roof = {"kernel": "bsi_forward_kernel", "bound": "hbm", "achieved": round(fwd_gbs, 1),
+                "peak": hbm_peak, "unit": "GB/s", "frac": round(fwd_gbs / hbm_peak, 4),
+                "traffic": ncu_traffic("bsi_forward_kernel"),
+                "algorithmic_bytes_per_launch": fwd_bytes, "avg_launch_ms": round(fwd_ms, 5),
+                "peak_kind": f"{peak_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        roof = {"kernel": "bsi_field_adjoint (partials + reduce)", "bound": "hbm",
+                "achieved": round(adj_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(adj_gbs / hbm_peak, 4), "traffic": ncu_traffic("bsi_adjoint_partials_kernel"),
+                "algorithmic_bytes_per_launch": adj_bytes, "avg_launch_ms": round(adj_ms, 5),
+                "peak_kind": f"{peak_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)"}
+
+    extras = {}
+    if not args.no_extras:
+        extras = run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_peak)
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "volume_zyx": list(shape), "spacing_zyx": list(spacing),
+                   "voxels_per_step_per_gpu": nvox, "step": "bsi_field_forward + bsi_field_adjoint",
+                   "l2": "inputs larger than L2 (field 944 MB written, voxel gradient 944 MB read per step)",
+                   "parallelism": f"{ws} independent volume(s), one per GPU"},
+        "fwd_ms": round(fwd_ms, 5), "adjoint_ms": round(adj_ms, 5),
+        "fwd_gbs": round(fwd_gbs, 1), "adjoint_gbs": round(adj_gbs, 1), "dominant_kernel": dominant,
+        "roofline": roof, "gpu_launches": launches,
+        "clocks": clk.summary(t0, t1),
+    }
+    out.update(extras)
+    if "e2e" not in out:
+        out["e2e"] = None
+    return out
+
+
+def time_fn(fn, s, iters, warm=3):
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(iters):
+        fn()
+    b.record(s)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / iters
+
+
+def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_peak):
+    import numpy as np
+    import torch
+
+    shape, spacing = CT_SHAPE, CT_SPACING
+    nvox = int(np.prod(shape))
+    res = {}
+    iters = 50
+
+    # forward-only FP32 / BF16 and adjoint-only on the CT volume
+    ms = time_fn(lambda: P.bsi_field_forward(phi, shape, spacing, out=field), s, iters)
+    b16 = torch.empty(shape + (3,), dtype=torch.bfloat16, device=dev)
+    ms16 = time_fn(lambda: P.bsi_field_forward(phi, shape, spacing, out=b16), s, iters)
+    msa = time_fn(lambda: P.bsi_field_adjoint(grad, spacing, out=dphi, workspace=work), s, iters)
+    res["components"] = {
+        "fwd_f32": {"gvox_s": round(nvox / ms / 1e6, 2), "ms": round(ms, 5),
+                    "gbs": round(model.forward_bytes(shape, spacing) / ms / 1e6, 1)},
+        "fwd_bf16": {"gvox_s": round(nvox / ms16 / 1e6, 2), "ms": round(ms16, 5),
+                     "gbs": round(model.forward_bytes(shape, spacing, 2) / ms16 / 1e6, 1)},
+        "adjoint": {"gvox_s": round(nvox / msa / 1e6, 2), "ms": round(msa, 5),
+                    "gbs": round(model.adjoint_bytes(shape, spacing) / msa / 1e6, 1)},
+    }
+    del b16
+
+    # 512^3 spacing sweep (forward FP32)
+    sweep = {}
+    big = (512, 512, 512)
+    out = torch.empty(big + (3,), device=dev)
+    for sp in [(3, 3, 3), (5, 5, 5), (6, 5, 4), (8, 8, 8)]:
+        ph = torch.from_numpy(synth.uniform_phi(big, sp, -4, 4, seed=3)).to(dev)
+        t = time_fn(lambda: P.bsi_field_forward(ph, big, sp, out=out), s, 20)
+        gbs = model.forward_bytes(big, sp) / t / 1e6
+        sweep["x".join(str(v) for v in sp[::-1])] = {
+            "gvox_s": round(512 ** 3 / t / 1e6, 2), "ms": round(t, 5), "gbs": round(gbs, 1),
+            "frac_of_hbm": round(gbs / hbm_peak, 4)}
+    res["sweep_512cubed_fwd"] = sweep
+    del out
+
+    # 64-volume uneven batch, forward + adjoint, replayed as one CUDA graph
+    geoms = synth.batch_geometries(64, seed=5)
+    shapes = [g[0] for g in geoms]
+    spacings = [g[1] for g in geoms]
+    bvox = sum(int(np.prod(x)) for x in shapes)
+    phis = [torch.from_numpy(synth.uniform_phi(a, b, -3, 3, seed=500 + i)).to(dev) for i, (a, b) in enumerate(geoms)]
+    grads = [torch.randn(a + (3,), device=dev) for a in shapes]
+    outs = [torch.empty(a + (3,), device=dev) for a in shapes]
+    dps = [torch.empty_like(p) for p in phis]
+    bws = torch.empty(P.bsi_batched_adjoint_workspace_bytes(shapes, spacings), dtype=torch.uint8, device=dev)
+
+    def bstep():
+        P.bsi_field_forward_batched(phis, shapes, spacings, outs=outs)
+        P.bsi_field_adjoint_batched(grads, spacings, outs=dps, workspace=bws)
+
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(s)
+    with torch.cuda.stream(side):
+        bstep()
+    s.wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        bstep()
+    tb = time_fn(g.replay, s, 20)
+    tbf = time_fn(lambda: P.bsi_field_forward_batched(phis, shapes, spacings, outs=outs), s, 20)
+    res["batched_64"] = {"gvox_s_fwd_adj": round(bvox / tb / 1e6, 2), "ms_fwd_adj": round(tb, 5),
+                         "gvox_s_fwd": round(bvox / tbf / 1e6, 2), "voxels": bvox,
+                         "vs_single_volume_fwd": round((bvox / tbf) / (nvox / ms), 3),
+                         "launches_per_step": 3, "cuda_graph": True}
+    del phis, grads, outs, dps, bws, g
+
+    # end to end through the public API with host buffers: H2D of phi and the voxel
+    # gradient, forward + adjoint, D2H of the field and the grid gradient, every step
+    phi_h = phi.cpu().pin_memory()
+    grad_h = grad.cpu().pin_memory()
+    field_h = torch.empty(field.shape, dtype=field.dtype).pin_memory()
+    dphi_h = torch.empty(dphi.shape, dtype=dphi.dtype).pin_memory()
+    phi_d, grad_d = torch.empty_like(phi), torch.empty_like(grad)
+
+    def e2e():
+        phi_d.copy_(phi_h, non_blocking=True)
+        grad_d.copy_(grad_h, non_blocking=True)
+        P.bsi_field_forward(phi_d, shape, spacing, out=field)
+        P.bsi_field_adjoint(grad_d, spacing, out=dphi, workspace=work)
+        field_h.copy_(field, non_blocking=True)
+        dphi_h.copy_(dphi, non_blocking=True)
+
+    te = time_fn(e2e, s, 10)
+    h2d = phi_h.numel() * 4 + grad_h.numel() * 4
+    d2h = field_h.numel() * 4 + dphi_h.numel() * 4
+    res["e2e"] = {"value": round(nvox / te / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                  "d2h_bytes_per_step": d2h, "ms_per_step": round(te, 4)}
+    return res
+
+
+# ------------------------------------------------------------------ oracle legs
+
+def oracle_slab_rate(budget_s, shape=CT_SHAPE, spacing=CT_SPACING, seed=2):
+    """Times the FP64 oracle (forward + adjoint, all host cores) on a z-slab of the
+    workload sized to ~budget_s seconds; returns (gvox_s, cores, sample text)."""
+    import numpy as np
+
+    import oracle
+    from paper_2004_05962_gb300 import synth
+
+    Z, Y, X = shape
+    dz = spacing[0]
+    phi = synth.gaussian_random_phi(shape, spacing, 3.0, 2.0, seed=seed)
+    rng = np.random.default_rng(seed)
+
+    def run(zs):
+        sub = (zs, Y, X)
+        nzs = -(-zs // dz) + 3
+        ph = np.ascontiguousarray(phi[:nzs])
+        g = rng.standard_normal(sub + (3,), dtype=np.float32)
+        t = time.perf_counter()
+        oracle.forward(ph, sub, spacing)
+        oracle.adjoint(g, spacing)
+        return time.perf_counter() - t
+
+    t1 = run(1)
+    zs = int(max(1, min(Z, budget_s / max(t1, 1e-6))))
+    t = run(zs)
+    vox = zs * Y * X
+    cores = oracle.threads()
+    return vox / t / 1e9, cores, f"forward + adjoint of a {X}x{Y}x{zs} z-slab (of {Z}) of the same workload, {t:.1f} s"
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    import numpy as np
+
+    import oracle
+    from paper_2004_05962_gb300 import synth
+
+    shape, spacing = CT_SHAPE, CT_SPACING
+    Z, Y, X = shape
+    per_step = max(0.5, 150.0 / max(1, args.steps + args.warmup))
+    phi = synth.gaussian_random_phi(shape, spacing, 3.0, 2.0, seed=2)
+    rng = np.random.default_rng(4)
+
+    def run(zs):
+        sub = (zs, Y, X)
+        nzs = -(-zs // spacing[0]) + 3
+        g = rng.standard_normal(sub + (3,), dtype=np.float32)
+        t = time.perf_counter()
+        oracle.forward(np.ascontiguousarray(phi[:nzs]), sub, spacing)
+        oracle.adjoint(g, spacing)
+        return time.perf_counter() - t
+
+    t1 = run(1)
+    zs = int(max(1, min(Z, per_step / max(t1, 1e-6))))
+    for _ in range(args.warmup):
+        run(zs)
+    times = [run(zs) for _ in range(args.steps)]
+    tot = sum(times)
+    vox = zs * Y * X
+    value = args.steps * vox / tot / 1e9
+    cores = oracle.threads()
+    sample = f"forward + adjoint of a {X}x{Y}x{zs} z-slab (of {Z}) per step"
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "volume_zyx": list(shape), "spacing_zyx": list(spacing),
+                       "reference": "FP64 CPU oracle of Eq. 1 and its transpose (the paper ships no code)"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out = run_ours(args, ws, rank, local)
+    if rank == 0:
+        if ws == 1 and not args.no_extras:
+            v, cores, sample = oracle_slab_rate(args.cpu_seconds)
+            out["cpu_baseline"] = {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                                   "sample": sample}
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

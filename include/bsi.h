@@ -1,0 +1,169 @@
+/*
+ * bsi.h -- C ABI of the GB300 (sm_103a) cubic B-spline interpolation library.
+ *
+ * The library turns a free-form-deformation control grid into the dense
+ * 3-channel displacement field of a volume (the "BSI transformation" of
+ * Eq. 1, Sec. 2.1 of Zachariadis et al., "Accelerating B-spline Interpolation
+ * on GPUs: Application to Medical Image Registration"), and applies the
+ * transpose of that map to a voxel gradient (the gather of dL/du back onto the
+ * control points that every gradient step of the registration loop needs).
+ *
+ * Definitions shared by every call
+ * --------------------------------
+ *   Volume X x Y x Z voxels, integer voxel coordinates, x fastest.
+ *   Spacing dx, dy, dz: control-point spacing in voxels (Sec. 2.1), 1..64.
+ *   Control grid nx x ny x nz with nx = ceil(X/dx) + 3 (likewise ny, nz):
+ *   the paper's neighbourhood index i = floor(x/dx) - 1 is stored at column
+ *   i + 1, so the grid carries one border point below and two above and
+ *   every 4x4x4 neighbourhood is in range.
+ *   B_0..B_3 are the uniform cubic B-spline blending functions.
+ *
+ *   field[z][y][x][c] = sum_{l,m,n=0..3} B_l(u) B_m(v) B_n(w)
+ *                         phi[fz+n][fy+m][fx+l][c]
+ *   fx = floor(x/dx), u = x/dx - fx   (likewise fy, v and fz, w), c = 0,1,2.
+ *
+ * Layouts (all row-major, channel-last, channel order x, y, z):
+ *   phi, grad_phi      float [nz][ny][nx][3]          (FP32)
+ *   field, grad_field  [Z][Y][X][3], FP32 or BF16 field, FP32 grad_field
+ *
+ * Conventions
+ * -----------
+ *   - Every buffer is device memory owned by the caller.  The library never
+ *     allocates, frees or synchronises inside these calls, so every call may
+ *     be captured in a CUDA graph; work is enqueued on `stream`.
+ *   - Arguments are validated on the host before anything is enqueued; a
+ *     non-BSI_OK return means nothing was launched.  A CUDA launch failure is
+ *     BSI_ERR_CUDA (see bsi_last_cuda_error()).  No call aborts or throws.
+ *   - Pointers need natural alignment only (4 bytes for FP32 arrays, 2 for a
+ *     BF16 field); any such base address is accepted.
+ *   - Results are deterministic: the adjoint sums its partials in a fixed
+ *     order and uses no atomics.
+ */
+#ifndef BSI_H
+#define BSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* bsi_stream_t;
+
+typedef enum {
+    BSI_OK = 0,
+    BSI_ERR_NULL = 1,          /* a required pointer is NULL */
+    BSI_ERR_DIMS = 2,          /* X, Y or Z negative or above BSI_MAX_DIM */
+    BSI_ERR_SPACING = 3,       /* dx, dy or dz outside 1..BSI_MAX_SPACING */
+    BSI_ERR_GRID_MISMATCH = 4, /* geom.nx/ny/nz differ from ceil(X/dx)+3 ... */
+    BSI_ERR_DTYPE = 5,         /* unknown bsi_dtype */
+    BSI_ERR_ALIGN = 6,         /* pointer not naturally aligned */
+    BSI_ERR_WORKSPACE = 7,     /* workspace NULL or smaller than required */
+    BSI_ERR_CUDA = 8,          /* a CUDA runtime call failed */
+    BSI_ERR_DEVICE_STATUS = 9, /* a kernel recorded an error (bsi_check_device_status) */
+    BSI_ERR_BATCH = 10         /* n < 0, or instances == NULL with n > 0 */
+} bsi_status;
+
+typedef enum { BSI_F32 = 0, BSI_BF16 = 1 } bsi_dtype;
+
+#define BSI_MAX_SPACING 64
+#define BSI_MAX_DIM (1 << 20)
+
+/* Geometry of one volume and its control grid.  nx, ny, nz state the grid the
+ * caller allocated; they must equal ceil(X/dx)+3 etc. (bsi_geom_init fills them). */
+typedef struct {
+    int64_t X, Y, Z;     /* volume size in voxels, 0..BSI_MAX_DIM each */
+    int32_t dx, dy, dz;  /* control-point spacing in voxels, 1..BSI_MAX_SPACING */
+    int32_t reserved;    /* set to 0 */
+    int64_t nx, ny, nz;  /* control-grid dims */
+} bsi_geom;
+
+/* Fills g from the volume size and spacing (grid dims derived).  Returns
+ * BSI_ERR_DIMS / BSI_ERR_SPACING for out-of-range values, BSI_ERR_NULL for g==NULL. */
+bsi_status bsi_geom_init(bsi_geom* g, int64_t X, int64_t Y, int64_t Z, int32_t dx, int32_t dy,
+                         int32_t dz);
+
+/* Forward BSI (Eq. 1, Sec. 2.1): writes the dense field from the control grid.
+ *   phi   : device, FP32 [nz][ny][nx][3], read only
+ *   field : device, [Z][Y][X][3] of out_dtype (BF16: round to nearest even of
+ *           the FP32 result), fully overwritten
+ * An empty volume (X, Y or Z == 0) launches nothing and returns BSI_OK. */
+bsi_status bsi_field_forward(const bsi_geom* g, const float* phi, void* field, bsi_dtype out_dtype,
+                             bsi_stream_t stream);
+
+/* Workspace bytes bsi_field_adjoint needs for geometry g (0 for an empty volume). */
+size_t bsi_adjoint_workspace_bytes(const bsi_geom* g);
+
+/* Adjoint BSI: the transpose of Eq. 1 applied to a voxel gradient,
+ *   grad_phi[g][c] = sum over voxels x of W(x, g) * grad_field[x][c],
+ * W(x, g) being the Eq. 1 weight of control point g at voxel x.  This is the
+ * gradient of any loss L(field) with respect to phi, given dL/dfield.
+ *   grad_field : device, FP32 [Z][Y][X][3], read only
+ *   grad_phi   : device, FP32 [nz][ny][nx][3], fully overwritten (not accumulated)
+ *   workspace  : device scratch of at least bsi_adjoint_workspace_bytes(g)
+ *                bytes, 16-byte aligned (BSI_ERR_ALIGN otherwise); contents
+ *                on entry are ignored.  May be NULL when the size is 0.
+ * Two kernels: per-warp partial sums over tiles, then a fixed-order reduce. */
+bsi_status bsi_field_adjoint(const bsi_geom* g, const float* grad_field, float* grad_phi,
+                             void* workspace, size_t workspace_bytes, bsi_stream_t stream);
+
+/* One volume of a batch.  Unused pointers (field/phi for an adjoint-only call,
+ * grad_field/grad_phi for a forward-only call) may be NULL. */
+typedef struct {
+    bsi_geom geom;
+    const float* phi;         /* forward input  FP32 [nz][ny][nx][3] */
+    void* field;              /* forward output [Z][Y][X][3], batch out_dtype */
+    const float* grad_field;  /* adjoint input  FP32 [Z][Y][X][3] */
+    float* grad_phi;          /* adjoint output FP32 [nz][ny][nx][3] */
+} bsi_instance;
+
+/* Batched forward over n volumes of uneven size and spacing (a registration
+ * batch): one persistent launch walks the tiles of every volume; instances are
+ * passed by value in the kernel parameters (up to 64 per launch, larger
+ * batches are split), so no device copy of the descriptors is needed and the
+ * call is capturable.  `inst` is host memory, read during the call only. */
+bsi_status bsi_field_forward_batched(const bsi_instance* inst, int n, bsi_dtype out_dtype,
+                                     bsi_stream_t stream);
+
+/* Workspace bytes bsi_field_adjoint_batched needs for these n instances. */
+size_t bsi_batched_adjoint_workspace_bytes(const bsi_instance* inst, int n);
+
+/* Batched adjoint over n volumes: one persistent partial-sum launch over all
+ * volumes' tiles, then one reduce launch; grad_phi of every instance is
+ * overwritten. */
+bsi_status bsi_field_adjoint_batched(const bsi_instance* inst, int n, void* workspace,
+                                     size_t workspace_bytes, bsi_stream_t stream);
+
+/* Static string naming a status code. */
+const char* bsi_status_string(bsi_status s);
+
+/* Message of the last CUDA error seen by this thread's calls ("" if none). */
+const char* bsi_last_cuda_error(void);
+
+/* Reads and clears the current device's kernel error word, synchronising
+ * `stream` first (the one call that synchronises).  *flags receives the
+ * word (0: no kernel recorded an error).  Returns BSI_ERR_DEVICE_STATUS if
+ * it was non-zero, BSI_ERR_CUDA if the read failed. */
+bsi_status bsi_check_device_status(bsi_stream_t stream, uint32_t* flags);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int bsi_version(void);
+
+/* Host-only diagnostic, no CUDA call: plans the launches of a batched call of
+ * kind op (0 forward FP32, 1 forward BF16, 2 adjoint) exactly as the entry
+ * points do, and checks with the kernels' own index functions that every
+ * global read and write lies inside its buffer and every staging copy fits
+ * its shared-memory buffer.  With cover != 0 it also checks that the forward
+ * writes each voxel exactly once and that the adjoint reduce reads only
+ * partial sums its first kernel writes (host memory ~ volume size).
+ * Returns the number of violations (0: all in range); the first one is
+ * described in msg (may be NULL). */
+int bsi_selfcheck_ranges(const bsi_instance* inst, int n, int op, int cover, char* msg, size_t msg_len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSI_H */

@@ -1,0 +1,21 @@
+"""GB300-native (sm_103a) cubic B-spline interpolation of FFD control grids.
+
+The C ABI is ``include/bsi.h``; ``bsi`` is its Python binding (same names),
+``autograd.field`` the differentiable wrapper, ``synth`` the seeded workload
+generators and ``model`` the traffic / operation-count models.
+"""
+from .bsi import (  # noqa: F401
+    BsiError,
+    BsiLibraryMissing,
+    bsi_adjoint_workspace_bytes,
+    bsi_batched_adjoint_workspace_bytes,
+    bsi_check_device_status,
+    bsi_field_adjoint,
+    bsi_field_adjoint_batched,
+    bsi_field_forward,
+    bsi_field_forward_batched,
+    bsi_selfcheck_ranges,
+    grid_shape,
+    library,
+)
+from .autograd import BSIField, field  # noqa: F401

@@ -1,0 +1,290 @@
+"""Python binding of the C ABI in include/bsi.h (ctypes; argument marshalling only).
+
+Every computation runs in the sm_103a kernels of ``_build/libbsi_gb300.so``;
+this module only checks tensor shapes and dtypes, builds the C structs and
+passes raw device pointers and the current CUDA stream.  PyTorch supplies
+device memory and streams.  There is no CPU fallback: if the library is
+missing every call raises ``BsiLibraryMissing``.
+
+Python shapes follow array order: ``shape = (Z, Y, X)`` voxels and
+``spacing = (dz, dy, dx)`` voxels; a control grid is a float32 tensor
+``[nz, ny, nx, 3]`` and a field ``[Z, Y, X, 3]`` (float32 or bfloat16).
+The function names are those of the C entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+BSI_F32, BSI_BF16 = 0, 1
+STATUS = {
+    0: "BSI_OK", 1: "BSI_ERR_NULL", 2: "BSI_ERR_DIMS", 3: "BSI_ERR_SPACING",
+    4: "BSI_ERR_GRID_MISMATCH", 5: "BSI_ERR_DTYPE", 6: "BSI_ERR_ALIGN", 7: "BSI_ERR_WORKSPACE",
+    8: "BSI_ERR_CUDA", 9: "BSI_ERR_DEVICE_STATUS", 10: "BSI_ERR_BATCH",
+}
+
+
+class BsiLibraryMissing(RuntimeError):
+    pass
+
+
+class BsiError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {STATUS.get(status, status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class BsiGeom(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_int64), ("Y", ctypes.c_int64), ("Z", ctypes.c_int64),
+                ("dx", ctypes.c_int32), ("dy", ctypes.c_int32), ("dz", ctypes.c_int32),
+                ("reserved", ctypes.c_int32),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64)]
+
+
+class BsiInstance(ctypes.Structure):
+    _fields_ = [("geom", BsiGeom), ("phi", ctypes.c_void_p), ("field", ctypes.c_void_p),
+                ("grad_field", ctypes.c_void_p), ("grad_phi", ctypes.c_void_p)]
+
+
+_LIBS: dict = {}
+_USE_CHECKED = os.environ.get("BSI_CHECKED", "0") == "1"
+
+
+def set_checked(flag: bool) -> None:
+    """Routes the entry points of this module to the bounds-checked build
+    (``True``) or the release build (``False``)."""
+    global _USE_CHECKED
+    _USE_CHECKED = bool(flag)
+
+
+def library(checked: bool | None = None) -> ctypes.CDLL:
+    """The loaded C library.  ``checked`` (default: env BSI_CHECKED=1, or the last
+    ``set_checked``) selects the bounds-checked build."""
+    if checked is None:
+        checked = _USE_CHECKED
+    if checked in _LIBS:
+        return _LIBS[checked]
+    path = _build.lib_path(checked)
+    if not path.exists():
+        raise BsiLibraryMissing(
+            f"{path} not found: build it with `python -m paper_2004_05962_gb300.build"
+            f"{' --checked' if checked else ''}` (or __graft_entry__.build()).  "
+            "There is no CPU fallback.")
+    lib = ctypes.CDLL(str(path))
+    vp, i32, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    G = ctypes.POINTER(BsiGeom)
+    I = ctypes.POINTER(BsiInstance)
+    sig = {
+        "bsi_geom_init": (i32, [G, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                                ctypes.c_int32, ctypes.c_int32]),
+        "bsi_field_forward": (i32, [G, vp, vp, i32, vp]),
+        "bsi_adjoint_workspace_bytes": (sz, [G]),
+        "bsi_field_adjoint": (i32, [G, vp, vp, vp, sz, vp]),
+        "bsi_field_forward_batched": (i32, [I, i32, i32, vp]),
+        "bsi_batched_adjoint_workspace_bytes": (sz, [I, i32]),
+        "bsi_field_adjoint_batched": (i32, [I, i32, vp, sz, vp]),
+        "bsi_status_string": (ctypes.c_char_p, [i32]),
+        "bsi_last_cuda_error": (ctypes.c_char_p, []),
+        "bsi_check_device_status": (i32, [vp, ctypes.POINTER(ctypes.c_uint32)]),
+        "bsi_version": (i32, []),
+        "bsi_selfcheck_ranges": (i32, [I, i32, i32, i32, ctypes.c_char_p, sz]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIBS[checked] = lib
+    return lib
+
+
+def exported_symbols():
+    return ["bsi_geom_init", "bsi_field_forward", "bsi_adjoint_workspace_bytes", "bsi_field_adjoint",
+            "bsi_field_forward_batched", "bsi_batched_adjoint_workspace_bytes",
+            "bsi_field_adjoint_batched", "bsi_status_string", "bsi_last_cuda_error",
+            "bsi_check_device_status", "bsi_version", "bsi_selfcheck_ranges"]
+
+
+# ---------------------------------------------------------------- helpers
+
+def grid_shape(shape, spacing):
+    """Control-grid dims (nz, ny, nx) = ceil(N/d) + 3 per axis."""
+    Z, Y, X = (int(s) for s in shape)
+    dz, dy, dx = (int(s) for s in spacing)
+    return (-(-Z // dz) + 3, -(-Y // dy) + 3, -(-X // dx) + 3)
+
+
+def make_geom(shape, spacing) -> BsiGeom:
+    Z, Y, X = (int(s) for s in shape)
+    dz, dy, dx = (int(s) for s in spacing)
+    g = BsiGeom()
+    st = library().bsi_geom_init(ctypes.byref(g), X, Y, Z, dx, dy, dz)
+    if st:
+        raise BsiError(st, "bsi_geom_init", f"shape={shape} spacing={spacing}")
+    return g
+
+
+def _stream(stream, device) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return int(stream.cuda_stream)
+
+
+def _check(st, where):
+    if st:
+        detail = library().bsi_last_cuda_error().decode() if st == 8 else ""
+        raise BsiError(st, where, detail)
+
+
+def _need(t, name, dtype, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _out_dtype_code(dtype):
+    if dtype == torch.float32:
+        return BSI_F32
+    if dtype == torch.bfloat16:
+        return BSI_BF16
+    raise ValueError(f"field dtype must be float32 or bfloat16, got {dtype}")
+
+
+# ---------------------------------------------------------------- entry points
+
+def bsi_field_forward(phi, shape, spacing, out=None, out_dtype=torch.float32, stream=None):
+    """Dense field [Z, Y, X, 3] from the control grid ``phi`` [nz, ny, nx, 3] (Eq. 1)."""
+    shape = tuple(int(s) for s in shape)
+    _need(phi, "phi", torch.float32, grid_shape(shape, spacing) + (3,))
+    if out is None:
+        out = torch.empty(shape + (3,), dtype=out_dtype, device=phi.device)
+    _need(out, "out", out.dtype, shape + (3,))
+    g = make_geom(shape, spacing)
+    st = library().bsi_field_forward(ctypes.byref(g), phi.data_ptr(), out.data_ptr(),
+                                     _out_dtype_code(out.dtype), _stream(stream, phi.device))
+    _check(st, "bsi_field_forward")
+    return out
+
+
+def bsi_adjoint_workspace_bytes(shape, spacing) -> int:
+    g = make_geom(shape, spacing)
+    return int(library().bsi_adjoint_workspace_bytes(ctypes.byref(g)))
+
+
+def _workspace(nbytes, device, workspace):
+    if nbytes == 0:
+        return workspace, 0
+    if workspace is None:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    if not workspace.is_cuda or workspace.numel() * workspace.element_size() < nbytes:
+        raise ValueError(f"workspace must be a CUDA tensor of at least {nbytes} bytes")
+    return workspace, workspace.numel() * workspace.element_size()
+
+
+def bsi_field_adjoint(grad_field, spacing, out=None, workspace=None, stream=None):
+    """Transpose of Eq. 1: control-grid gradient [nz, ny, nx, 3] from a voxel
+    gradient [Z, Y, X, 3] (float32).  ``workspace`` (uint8 CUDA tensor) is
+    allocated through PyTorch when not given."""
+    _need(grad_field, "grad_field", torch.float32)
+    if grad_field.dim() != 4 or grad_field.shape[3] != 3:
+        raise ValueError("grad_field must be [Z, Y, X, 3]")
+    shape = tuple(grad_field.shape[:3])
+    grid = grid_shape(shape, spacing)
+    if out is None:
+        out = torch.empty(grid + (3,), dtype=torch.float32, device=grad_field.device)
+    _need(out, "out", torch.float32, grid + (3,))
+    g = make_geom(shape, spacing)
+    need = int(library().bsi_adjoint_workspace_bytes(ctypes.byref(g)))
+    ws, wsb = _workspace(need, grad_field.device, workspace)
+    st = library().bsi_field_adjoint(ctypes.byref(g), grad_field.data_ptr(), out.data_ptr(),
+                                     ws.data_ptr() if ws is not None else None, wsb,
+                                     _stream(stream, grad_field.device))
+    _check(st, "bsi_field_adjoint")
+    return out
+
+
+def _instances(shapes, spacings, phis=None, fields=None, grads=None, dphis=None):
+    n = len(shapes)
+    arr = (BsiInstance * max(n, 1))()
+    for i in range(n):
+        arr[i].geom = make_geom(shapes[i], spacings[i])
+        arr[i].phi = phis[i].data_ptr() if phis is not None else None
+        arr[i].field = fields[i].data_ptr() if fields is not None else None
+        arr[i].grad_field = grads[i].data_ptr() if grads is not None else None
+        arr[i].grad_phi = dphis[i].data_ptr() if dphis is not None else None
+    return arr
+
+
+def bsi_field_forward_batched(phis, shapes, spacings, outs=None, out_dtype=torch.float32, stream=None):
+    """Forward over a batch of volumes of uneven size and spacing (persistent launch)."""
+    n = len(phis)
+    shapes = [tuple(int(s) for s in sh) for sh in shapes]
+    for i in range(n):
+        _need(phis[i], f"phis[{i}]", torch.float32, grid_shape(shapes[i], spacings[i]) + (3,))
+    if outs is None:
+        outs = [torch.empty(shapes[i] + (3,), dtype=out_dtype, device=phis[i].device) for i in range(n)]
+    dt = outs[0].dtype if n else out_dtype
+    for i in range(n):
+        _need(outs[i], f"outs[{i}]", dt, shapes[i] + (3,))
+    arr = _instances(shapes, spacings, phis=phis, fields=outs)
+    dev = phis[0].device if n else torch.device("cuda")
+    st = library().bsi_field_forward_batched(arr, n, _out_dtype_code(dt), _stream(stream, dev))
+    _check(st, "bsi_field_forward_batched")
+    return outs
+
+
+def bsi_batched_adjoint_workspace_bytes(shapes, spacings) -> int:
+    arr = _instances([tuple(s) for s in shapes], spacings)
+    return int(library().bsi_batched_adjoint_workspace_bytes(arr, len(shapes)))
+
+
+def bsi_field_adjoint_batched(grads, spacings, outs=None, workspace=None, stream=None):
+    """Adjoint over a batch: one partial-sum launch over all volumes, one reduce."""
+    n = len(grads)
+    shapes = []
+    for i in range(n):
+        _need(grads[i], f"grads[{i}]", torch.float32)
+        shapes.append(tuple(grads[i].shape[:3]))
+    if outs is None:
+        outs = [torch.empty(grid_shape(shapes[i], spacings[i]) + (3,), dtype=torch.float32,
+                            device=grads[i].device) for i in range(n)]
+    for i in range(n):
+        _need(outs[i], f"outs[{i}]", torch.float32, grid_shape(shapes[i], spacings[i]) + (3,))
+    arr = _instances(shapes, spacings, grads=grads, dphis=outs)
+    dev = grads[0].device if n else torch.device("cuda")
+    need = int(library().bsi_batched_adjoint_workspace_bytes(arr, n))
+    ws, wsb = _workspace(need, dev, workspace)
+    st = library().bsi_field_adjoint_batched(arr, n, ws.data_ptr() if ws is not None else None, wsb,
+                                             _stream(stream, dev))
+    _check(st, "bsi_field_adjoint_batched")
+    return outs
+
+
+def bsi_check_device_status(stream=None, device=None) -> int:
+    """Synchronises the stream and returns (and clears) the kernel error word."""
+    flags = ctypes.c_uint32(0)
+    st = library().bsi_check_device_status(_stream(stream, device), ctypes.byref(flags))
+    if st not in (0, 9):
+        _check(st, "bsi_check_device_status")
+    return int(flags.value)
+
+
+def bsi_selfcheck_ranges(shapes, spacings, op: str = "forward", cover: bool = True):
+    """Host-only range check of every kernel access for a planned call (no GPU).
+    ``op`` is "forward", "forward_bf16" or "adjoint".  Returns (violations, message)."""
+    code = {"forward": 0, "forward_bf16": 1, "adjoint": 2}[op]
+    arr = _instances([tuple(s) for s in shapes], spacings)
+    buf = ctypes.create_string_buffer(256)
+    n = library().bsi_selfcheck_ranges(arr, len(shapes), code, int(cover), buf, 256)
+    return int(n), buf.value.decode()

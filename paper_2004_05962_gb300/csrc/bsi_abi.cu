@@ -1,0 +1,515 @@
+// bsi_abi.cu -- the C ABI declared in include/bsi.h: host-side validation,
+// launch planning and the host-only range self-check.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "bsi.h"
+#include "bsi_geometry.h"
+#include "bsi_launch.h"
+
+namespace bsi {
+
+// ----------------------------------------------------------- kernel facts
+
+cudaError_t kernel_facts(const void* kernel, int threads, int smem, KernelFacts* out) {
+    static std::mutex mu;
+    struct Key {
+        const void* k;
+        int dev, threads, smem;
+        bool operator==(const Key& o) const {
+            return k == o.k && dev == o.dev && threads == o.threads && smem == o.smem;
+        }
+    };
+    struct KeyHash {
+        size_t operator()(const Key& a) const {
+            return std::hash<const void*>()(a.k) ^ ((size_t)a.dev << 40) ^ ((size_t)a.threads << 20) ^
+                   (size_t)a.smem;
+        }
+    };
+    static std::unordered_map<Key, KernelFacts, KeyHash> cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const Key key{kernel, dev, threads, smem};
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    KernelFacts f;
+    e = cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f.ctas_per_sm, kernel, threads, (size_t)smem);
+    if (e != cudaSuccess) return e;
+    if (f.ctas_per_sm < 1) return cudaErrorInvalidConfiguration;
+    cache.emplace(key, f);
+    *out = f;
+    return cudaSuccess;
+}
+
+// ----------------------------------------------------------- planning
+
+constexpr int kDefaultZChunk = 4;
+
+static thread_local char t_cuda_msg[256] = "";
+
+static bsi_status cuda_fail(cudaError_t e) {
+    std::snprintf(t_cuda_msg, sizeof t_cuda_msg, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return BSI_ERR_CUDA;
+}
+
+static bsi_status check_geom(const bsi_geom* g) {
+    if (!g) return BSI_ERR_NULL;
+    if (g->X < 0 || g->Y < 0 || g->Z < 0 || g->X > BSI_MAX_DIM || g->Y > BSI_MAX_DIM || g->Z > BSI_MAX_DIM)
+        return BSI_ERR_DIMS;
+    if (g->dx < 1 || g->dy < 1 || g->dz < 1 || g->dx > BSI_MAX_SPACING || g->dy > BSI_MAX_SPACING ||
+        g->dz > BSI_MAX_SPACING)
+        return BSI_ERR_SPACING;
+    if (g->nx != cdiv(g->X, g->dx) + 3 || g->ny != cdiv(g->Y, g->dy) + 3 || g->nz != cdiv(g->Z, g->dz) + 3)
+        return BSI_ERR_GRID_MISMATCH;
+    return BSI_OK;
+}
+
+static bool empty_volume(const bsi_geom& g) { return g.X == 0 || g.Y == 0 || g.Z == 0; }
+
+static void fill_desc(InstDesc& d, const bsi_geom& g, bool adjoint, int zchunk) {
+    std::memset(&d, 0, sizeof d);
+    d.X = (int)g.X;
+    d.Y = (int)g.Y;
+    d.Z = (int)g.Z;
+    d.dx = g.dx;
+    d.dy = g.dy;
+    d.dz = g.dz;
+    d.nx = (int)g.nx;
+    d.ny = (int)g.ny;
+    d.nz = (int)g.nz;
+    const bool empty = empty_volume(g);
+    if (!empty) {
+        d.ncx = (int)cdiv(g.X, g.dx);
+        d.ncy = (int)cdiv(g.Y, g.dy);
+        d.ncz = (int)cdiv(g.Z, g.dz);
+    }
+    if (!adjoint) {
+        d.nxg = empty ? 0 : (int)cdiv(d.ncx, kGroupCells);
+        d.units = (long long)d.ncz * d.ncy * d.nxg;
+    } else {
+        d.zchunk = zchunk;
+        d.nxg = empty ? 0 : (int)cdiv(d.nx, kGroupCells);
+        d.nzc = empty ? 0 : (int)cdiv(d.ncz, zchunk);
+        d.units = (long long)d.nzc * d.ncy * d.nxg;
+    }
+}
+
+static long long adj_floats(const InstDesc& d) {
+    const long long f = d.units * adj_unit_floats(d);
+    return (f + 3) & ~3LL;  // keep every instance's partials 16-byte aligned
+}
+
+// A launch group: up to kMaxBatch instances that share a kernel variant.
+struct Group {
+    bool generic = false;
+    int dxmax = 1;
+    std::vector<InstDesc> inst;
+};
+
+// Splits instances into groups of one kernel variant (x-spacing <= 8 takes the
+// compile-time-specialised kernel, larger spacings the generic one), in caller
+// order, at most kMaxBatch per group; fills unit/point prefixes and partial offsets.
+static std::vector<Group> plan(const std::vector<InstDesc>& all, long long* ws_floats) {
+    std::vector<Group> out;
+    long long off = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool generic = pass == 1;
+        Group cur;
+        cur.generic = generic;
+        for (const InstDesc& d0 : all) {
+            if ((d0.dx > kMaxSpecializedDx) != generic) continue;
+            InstDesc d = d0;
+            d.part_off = off;
+            off += adj_floats(d);
+            cur.inst.push_back(d);
+            cur.dxmax = std::max(cur.dxmax, d.dx);
+            if ((int)cur.inst.size() == kMaxBatch) {
+                out.push_back(cur);
+                cur.inst.clear();
+                cur.dxmax = 1;
+            }
+        }
+        if (!cur.inst.empty()) out.push_back(cur);
+    }
+    for (Group& g : out) {
+        long long ub = 0, pb = 0;
+        for (InstDesc& d : g.inst) {
+            d.unit_begin = ub;
+            d.point_begin = pb;
+            ub += d.units;
+            pb += (long long)d.nx * d.ny * d.nz;
+        }
+    }
+    if (ws_floats) *ws_floats = off;
+    return out;
+}
+
+template <int MAXB>
+static void to_batch(const Group& g, Batch<MAXB>& b) {
+    std::memset(&b, 0, sizeof b);
+    b.n = (int)g.inst.size();
+    b.buf_bytes = stage_buf_bytes(g.generic ? g.dxmax : kMaxSpecializedDx);
+    for (int i = 0; i < b.n; ++i) {
+        b.inst[i] = g.inst[i];
+        b.total_units += g.inst[i].units;
+        b.total_points += (long long)g.inst[i].nx * g.inst[i].ny * g.inst[i].nz;
+    }
+}
+
+enum class Op { Forward, AdjointPartials, AdjointReduce };
+
+static cudaError_t run_group(const Group& g, Op op, bool bf16, float* part, long long ws_floats,
+                             cudaStream_t s) {
+    if (g.inst.size() == 1) {
+        Batch<1> b;
+        to_batch(g, b);
+        if (op == Op::Forward) return launch_forward(b, bf16, g.generic, s, nullptr);
+        if (op == Op::AdjointPartials) return launch_adjoint_partials(b, g.generic, part, ws_floats, s, nullptr);
+        return launch_adjoint_reduce(b, part, ws_floats, s, nullptr);
+    }
+    static thread_local Batch<kMaxBatch> b;  // ~9 KB: kept off the stack
+    to_batch(g, b);
+    if (op == Op::Forward) return launch_forward(b, bf16, g.generic, s, nullptr);
+    if (op == Op::AdjointPartials) return launch_adjoint_partials(b, g.generic, part, ws_floats, s, nullptr);
+    return launch_adjoint_reduce(b, part, ws_floats, s, nullptr);
+}
+
+static bool misaligned(const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) != 0; }
+
+static bsi_status check_instances(const bsi_instance* inst, int n, bool fwd, bool adj, bsi_dtype dt) {
+    if (n < 0 || (n > 0 && !inst)) return BSI_ERR_BATCH;
+    for (int i = 0; i < n; ++i) {
+        const bsi_status st = check_geom(&inst[i].geom);
+        if (st != BSI_OK) return st;
+        const bool empty = empty_volume(inst[i].geom);
+        if (fwd && !empty) {
+            if (!inst[i].phi || !inst[i].field) return BSI_ERR_NULL;
+            if (misaligned(inst[i].phi, 4) || misaligned(inst[i].field, dt == BSI_BF16 ? 2 : 4))
+                return BSI_ERR_ALIGN;
+        }
+        if (adj) {
+            if (!inst[i].grad_phi || (!empty && !inst[i].grad_field)) return BSI_ERR_NULL;
+            if (misaligned(inst[i].grad_phi, 4) || misaligned(inst[i].grad_field, 4)) return BSI_ERR_ALIGN;
+        }
+    }
+    return BSI_OK;
+}
+
+static std::vector<InstDesc> descs(const bsi_instance* inst, int n, bool adjoint) {
+    std::vector<InstDesc> v((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        fill_desc(v[(size_t)i], inst[i].geom, adjoint, kDefaultZChunk);
+        v[(size_t)i].phi = inst[i].phi;
+        v[(size_t)i].field = inst[i].field;
+        v[(size_t)i].grad = inst[i].grad_field;
+        v[(size_t)i].dphi = inst[i].grad_phi;
+    }
+    return v;
+}
+
+static bsi_status forward_impl(const bsi_instance* inst, int n, bsi_dtype dt, cudaStream_t s) {
+    if (dt != BSI_F32 && dt != BSI_BF16) return BSI_ERR_DTYPE;
+    bsi_status st = check_instances(inst, n, true, false, dt);
+    if (st != BSI_OK) return st;
+    std::vector<InstDesc> all = descs(inst, n, false);
+    all.erase(std::remove_if(all.begin(), all.end(), [](const InstDesc& d) { return d.units == 0; }), all.end());
+    for (const Group& g : plan(all, nullptr)) {
+        const cudaError_t e = run_group(g, Op::Forward, dt == BSI_BF16, nullptr, 0, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return BSI_OK;
+}
+
+static bsi_status adjoint_impl(const bsi_instance* inst, int n, void* ws, size_t ws_bytes, cudaStream_t s) {
+    bsi_status st = check_instances(inst, n, false, true, BSI_F32);
+    if (st != BSI_OK) return st;
+    long long ws_floats = 0;
+    const std::vector<Group> groups = plan(descs(inst, n, true), &ws_floats);
+    if ((size_t)ws_floats * sizeof(float) > ws_bytes) return BSI_ERR_WORKSPACE;
+    if (ws_floats > 0 && !ws) return BSI_ERR_WORKSPACE;
+    if (ws && misaligned(ws, 16)) return BSI_ERR_ALIGN;
+    float* part = static_cast<float*>(ws);
+    for (const Group& g : groups) {
+        cudaError_t e = run_group(g, Op::AdjointPartials, false, part, ws_floats, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    for (const Group& g : groups) {
+        cudaError_t e = run_group(g, Op::AdjointReduce, false, part, ws_floats, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return BSI_OK;
+}
+
+// ----------------------------------------------------------- self-check
+
+struct RangeChecker {
+    int bad = 0;
+    char msg[256] = "";
+    void fail(const char* what, long long a, long long b) {
+        if (!bad) std::snprintf(msg, sizeof msg, "%s (%lld, %lld)", what, a, b);
+        ++bad;
+    }
+};
+
+// Walks every unit of a forward launch plan and checks, with the kernels' own
+// index functions, that each read and write lies inside its buffer, that each
+// staging copy fits its shared-memory buffer, and (when `cover` is set) that
+// the rows of the units tile the field exactly once.
+static void check_forward_group(const Group& g, int es, RangeChecker& rc, bool cover) {
+    const int buf = stage_buf_bytes(g.generic ? g.dxmax : kMaxSpecializedDx);
+    for (const InstDesc& d : g.inst) {
+        const long long phi_elems = 3LL * d.nx * d.ny * d.nz;
+        const long long field_elems = 3LL * d.X * d.Y * d.Z;
+        std::vector<unsigned char> hit(cover ? (size_t)d.X * d.Y * d.Z : 0, 0);
+        for (long long ul = 0; ul < d.units; ++ul) {
+            const FwdUnit u = fwd_unit(d, ul);
+            if (u.ncell < 1 || u.nvox < 1) rc.fail("forward unit without tiles", ul, u.ncell);
+            for (int lane = 0; lane < kLanes; ++lane) {
+                const int col = u.cell0 + lane;
+                if (col >= d.nx) continue;
+                for (int n = 0; n < 4; ++n)
+                    for (int m = 0; m < 4; ++m) {
+                        const long long e = phi_elem(d, u.kz + n, u.jy + m, col);
+                        if (e < 0 || e + 3 > phi_elems) rc.fail("phi read", e, phi_elems);
+                    }
+                if (lane < u.ncell && lane * d.dx >= u.nvox) rc.fail("emitting lane past strip", lane, u.nvox);
+            }
+            const int z0 = u.kz * d.dz, zn = imin(d.dz, d.Z - z0);
+            const int y0 = u.jy * d.dy, yn = imin(d.dy, d.Y - y0);
+            if (15 + u.nvox * 3 * es > buf) rc.fail("staging overflow", u.nvox, buf);
+            for (int rz = 0; rz < zn; ++rz)
+                for (int ry = 0; ry < yn; ++ry) {
+                    const long long e0 = field_elem(d, z0 + rz, y0 + ry, u.x0);
+                    if (e0 < 0 || e0 + 3LL * u.nvox > field_elems) rc.fail("field write", e0, field_elems);
+                    if (cover)
+                        for (int x = 0; x < u.nvox; ++x) hit[(size_t)(e0 / 3 + x)]++;
+                }
+        }
+        if (cover)
+            for (size_t i = 0; i < hit.size(); ++i)
+                if (hit[i] != 1) {
+                    rc.fail("voxel written != once", (long long)i, hit[i]);
+                    break;
+                }
+    }
+}
+
+static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecker& rc, bool cover) {
+    const int buf = stage_buf_bytes(g.generic ? g.dxmax : kMaxSpecializedDx);
+    std::vector<unsigned char> written(cover ? (size_t)(ws_floats / 3 + 1) : 0, 0);
+    for (const InstDesc& d : g.inst) {
+        const long long field_elems = 3LL * d.X * d.Y * d.Z;
+        for (long long ul = 0; ul < d.units; ++ul) {
+            const AdjUnit u = adj_unit(d, ul);
+            if (u.kz1 <= u.kz0) rc.fail("adjoint unit without planes", ul, u.kz0);
+            if (15 + u.nvox * 12 > buf) rc.fail("staging overflow", u.nvox, buf);
+            for (int lane = 0; lane < kLanes; ++lane) {
+                const int cell = u.col0 - kHalo + lane;
+                const int nv = (cell >= 0 && cell < d.ncx) ? imin(d.dx, d.X - cell * d.dx) : 0;
+                const int xl = cell * d.dx - u.xs;
+                if (nv > 0 && (xl < 0 || xl + nv > u.nvox)) rc.fail("lane voxels outside strip", xl, u.nvox);
+                const int j = lane - kHalo;
+                if (j < 0 || u.col0 + j >= d.nx) continue;
+                for (int pz = 0; pz < u.kz1 - u.kz0 + kHalo; ++pz)
+                    for (int m = 0; m < 4; ++m) {
+                        const long long e = part_elem(d, ul, pz, m, j);
+                        if (e < 0 || e + 3 > ws_floats) rc.fail("partial write", e, ws_floats);
+                        else if (cover) written[(size_t)(e / 3)] = 1;
+                    }
+            }
+            for (int kz = u.kz0; kz < u.kz1; ++kz) {
+                const int z0 = kz * d.dz, zn = imin(d.dz, d.Z - z0);
+                const int y0 = u.jy * d.dy, yn = imin(d.dy, d.Y - y0);
+                for (int rz = 0; rz < zn; ++rz)
+                    for (int ry = 0; ry < yn; ++ry) {
+                        const long long e0 = field_elem(d, z0 + rz, y0 + ry, u.xs);
+                        if (e0 < 0 || e0 + 3LL * u.nvox > field_elems) rc.fail("grad read", e0, field_elems);
+                    }
+            }
+        }
+    }
+    // the reduce: every partial read lies in the workspace and was written by phase 1
+    for (const InstDesc& d : g.inst) {
+        for (int gz = 0; gz < d.nz; ++gz)
+            for (int gy = 0; gy < d.ny; ++gy)
+                for (int gx = 0; gx < d.nx; ++gx) {
+                    if (d.nzc <= 0) continue;
+                    const int xg = gx / kGroupCells, j = gx - xg * kGroupCells;
+                    const int zc_hi = imin(d.nzc - 1, gz / d.zchunk);
+                    const int zc_lo =
+                        gz - d.zchunk - kHalo + 1 > 0 ? (int)cdiv(gz - d.zchunk - kHalo + 1, d.zchunk) : 0;
+                    for (int zc = zc_lo; zc <= zc_hi; ++zc) {
+                        const int pz = gz - zc * d.zchunk;
+                        const int planes = imin(d.zchunk, d.ncz - zc * d.zchunk) + kHalo;
+                        if (pz >= planes) continue;
+                        for (int m = 0; m < 4; ++m) {
+                            const int jy = gy - m;
+                            if (jy < 0 || jy >= d.ncy) continue;
+                            const long long ul = ((long long)zc * d.ncy + jy) * d.nxg + xg;
+                            const long long e = part_elem(d, ul, pz, m, j);
+                            if (e < 0 || e + 3 > ws_floats) rc.fail("partial read", e, ws_floats);
+                            else if (cover && !written[(size_t)(e / 3)]) rc.fail("partial read before write", e, gx);
+                        }
+                    }
+                }
+    }
+}
+
+}  // namespace bsi
+
+using namespace bsi;
+
+extern "C" {
+
+bsi_status bsi_geom_init(bsi_geom* g, int64_t X, int64_t Y, int64_t Z, int32_t dx, int32_t dy, int32_t dz) {
+    if (!g) return BSI_ERR_NULL;
+    std::memset(g, 0, sizeof *g);
+    g->X = X;
+    g->Y = Y;
+    g->Z = Z;
+    g->dx = dx;
+    g->dy = dy;
+    g->dz = dz;
+    if (X < 0 || Y < 0 || Z < 0 || X > BSI_MAX_DIM || Y > BSI_MAX_DIM || Z > BSI_MAX_DIM) return BSI_ERR_DIMS;
+    if (dx < 1 || dy < 1 || dz < 1 || dx > BSI_MAX_SPACING || dy > BSI_MAX_SPACING || dz > BSI_MAX_SPACING)
+        return BSI_ERR_SPACING;
+    g->nx = cdiv(X, dx) + 3;
+    g->ny = cdiv(Y, dy) + 3;
+    g->nz = cdiv(Z, dz) + 3;
+    return BSI_OK;
+}
+
+bsi_status bsi_field_forward(const bsi_geom* g, const float* phi, void* field, bsi_dtype out_dtype,
+                             bsi_stream_t stream) {
+    if (!g) return BSI_ERR_NULL;
+    bsi_instance in;
+    std::memset(&in, 0, sizeof in);
+    in.geom = *g;
+    in.phi = phi;
+    in.field = field;
+    return forward_impl(&in, 1, out_dtype, reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t bsi_adjoint_workspace_bytes(const bsi_geom* g) {
+    if (check_geom(g) != BSI_OK) return 0;
+    InstDesc d;
+    fill_desc(d, *g, true, kDefaultZChunk);
+    return (size_t)adj_floats(d) * sizeof(float);
+}
+
+bsi_status bsi_field_adjoint(const bsi_geom* g, const float* grad_field, float* grad_phi, void* workspace,
+                             size_t workspace_bytes, bsi_stream_t stream) {
+    if (!g) return BSI_ERR_NULL;
+    bsi_instance in;
+    std::memset(&in, 0, sizeof in);
+    in.geom = *g;
+    in.grad_field = grad_field;
+    in.grad_phi = grad_phi;
+    return adjoint_impl(&in, 1, workspace, workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+bsi_status bsi_field_forward_batched(const bsi_instance* inst, int n, bsi_dtype out_dtype, bsi_stream_t stream) {
+    return forward_impl(inst, n, out_dtype, reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t bsi_batched_adjoint_workspace_bytes(const bsi_instance* inst, int n) {
+    if (n < 0 || (n > 0 && !inst)) return 0;
+    long long total = 0;
+    for (int i = 0; i < n; ++i) {
+        if (check_geom(&inst[i].geom) != BSI_OK) return 0;
+        InstDesc d;
+        fill_desc(d, inst[i].geom, true, kDefaultZChunk);
+        total += adj_floats(d);
+    }
+    return (size_t)total * sizeof(float);
+}
+
+bsi_status bsi_field_adjoint_batched(const bsi_instance* inst, int n, void* workspace, size_t workspace_bytes,
+                                     bsi_stream_t stream) {
+    return adjoint_impl(inst, n, workspace, workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+const char* bsi_status_string(bsi_status s) {
+    switch (s) {
+        case BSI_OK: return "BSI_OK";
+        case BSI_ERR_NULL: return "BSI_ERR_NULL: a required pointer is NULL";
+        case BSI_ERR_DIMS: return "BSI_ERR_DIMS: volume dimension out of range";
+        case BSI_ERR_SPACING: return "BSI_ERR_SPACING: spacing outside 1..64";
+        case BSI_ERR_GRID_MISMATCH: return "BSI_ERR_GRID_MISMATCH: grid dims differ from ceil(N/d)+3";
+        case BSI_ERR_DTYPE: return "BSI_ERR_DTYPE: unknown output dtype";
+        case BSI_ERR_ALIGN: return "BSI_ERR_ALIGN: pointer not naturally aligned";
+        case BSI_ERR_WORKSPACE: return "BSI_ERR_WORKSPACE: workspace missing or too small";
+        case BSI_ERR_CUDA: return "BSI_ERR_CUDA: a CUDA call failed";
+        case BSI_ERR_DEVICE_STATUS: return "BSI_ERR_DEVICE_STATUS: a kernel recorded an error";
+        case BSI_ERR_BATCH: return "BSI_ERR_BATCH: bad instance count or list";
+    }
+    return "unknown bsi_status";
+}
+
+const char* bsi_last_cuda_error(void) { return t_cuda_msg; }
+
+bsi_status bsi_check_device_status(bsi_stream_t stream, uint32_t* flags) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    static thread_local unsigned words[2];
+    cudaError_t e = forward_err_read_clear(&words[0], s);
+    if (e == cudaSuccess) e = adjoint_err_read_clear(&words[1], s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const uint32_t w = words[0] | words[1];
+    if (flags) *flags = w;
+    return w ? BSI_ERR_DEVICE_STATUS : BSI_OK;
+}
+
+int bsi_version(void) { return 100; }
+
+// Host-only: plans the launches of a batched call exactly as the entry points
+// do and checks every global and shared-memory range the kernels will touch
+// (see RangeChecker).  op: 0 forward F32, 1 forward BF16, 2 adjoint.  With
+// cover != 0 it also checks that forward rows tile each field exactly once and
+// that the reduce reads only partials phase 1 writes (memory ~ field size).
+// Returns the number of violations; the first is described in msg.
+int bsi_selfcheck_ranges(const bsi_instance* inst, int n, int op, int cover, char* msg, size_t msg_len) {
+    RangeChecker rc;
+    if (n < 0 || (n > 0 && !inst) || op < 0 || op > 2) {
+        rc.fail("bad arguments", n, op);
+    } else {
+        bool ok = true;
+        for (int i = 0; i < n; ++i) ok = ok && check_geom(&inst[i].geom) == BSI_OK;
+        if (!ok) {
+            rc.fail("invalid geometry", n, 0);
+        } else if (op < 2) {
+            std::vector<InstDesc> all = descs(inst, n, false);
+            all.erase(std::remove_if(all.begin(), all.end(), [](const InstDesc& d) { return d.units == 0; }),
+                      all.end());
+            for (const Group& g : plan(all, nullptr)) check_forward_group(g, op == 1 ? 2 : 4, rc, cover != 0);
+        } else {
+            long long ws = 0;
+            const std::vector<Group> groups = plan(descs(inst, n, true), &ws);
+            for (const Group& g : groups) check_adjoint_group(g, ws, rc, cover != 0);
+        }
+    }
+    if (msg && msg_len) {
+        std::strncpy(msg, rc.msg, msg_len - 1);
+        msg[msg_len - 1] = 0;
+    }
+    return rc.bad;
+}
+
+}  // extern "C"

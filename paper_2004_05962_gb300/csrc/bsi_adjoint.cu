@@ -1,0 +1,160 @@
+// bsi_adjoint.cu -- adjoint (transpose of Eq. 1) kernels and their launchers.
+//
+// Phase 1 (bsi_adjoint_partials_kernel): each warp unit walks a chunk of
+// tile-planes of one tile-row and one x-group and writes the complete-in-x,
+// partial-in-y/z sums of its (chunk+3) x 4 x 29 control points.
+// Phase 2 (bsi_adjoint_reduce_kernel): each control point sums the <= 2 x 4
+// partials that cover it, in a fixed order, and writes grad_phi.
+#include "bsi_kernels.cuh"
+#include "bsi_launch.h"
+
+namespace bsi {
+
+static __constant__ WeightTable c_lut = make_weight_table();
+static __device__ unsigned g_err;
+
+template <int MAXB, bool GENERIC>
+__global__ void __launch_bounds__(kThreads, 2)
+    bsi_adjoint_partials_kernel(const __grid_constant__ Batch<MAXB> b, float* __restrict__ part,
+                                long long ws_floats) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & (kLanes - 1);
+    const int warp = threadIdx.x >> 5;
+    unsigned char* stage = smem + (size_t)warp * 2 * b.buf_bytes;
+    const int wpc = blockDim.x >> 5;
+    const long long nwarps = (long long)gridDim.x * wpc;
+    int ii = 0, par = 0;
+    for (long long uu = (long long)blockIdx.x * wpc + warp; uu < b.total_units; uu += nwarps) {
+        while (ii + 1 < b.n && uu >= b.inst[ii + 1].unit_begin) ++ii;
+        const InstDesc& d = b.inst[ii];
+        const long long ul = uu - d.unit_begin;
+        if (GENERIC) {
+            adjoint_unit<0>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err);
+        } else {
+            switch (d.dx) {
+                case 1: adjoint_unit<1>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
+                case 2: adjoint_unit<2>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
+                case 3: adjoint_unit<3>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
+                case 4: adjoint_unit<4>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
+                case 5: adjoint_unit<5>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
+                case 6: adjoint_unit<6>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
+                case 7: adjoint_unit<7>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
+                default: adjoint_unit<8>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
+            }
+        }
+    }
+}
+
+// One thread per stored control point of every instance.  The units that
+// cover point (gx, gy, gz): x-group gx / 29 (columns are complete within a
+// unit), tile-rows jy = gy - m for m = 0..3, and the tile-plane chunks whose
+// plane window [chunk start, chunk start + planes + 3) contains gz.
+template <int MAXB>
+__global__ void __launch_bounds__(256)
+    bsi_adjoint_reduce_kernel(const __grid_constant__ Batch<MAXB> b, const float* __restrict__ part,
+                              long long ws_floats) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < b.total_points; p += stride) {
+        int lo = 0, hi = b.n - 1;  // last instance with point_begin <= p
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.inst[mid].point_begin <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        const InstDesc& d = b.inst[lo];
+        const long long pl = p - d.point_begin;
+        const int gx = (int)(pl % d.nx);
+        const long long t = pl / d.nx;
+        const int gy = (int)(t % d.ny);
+        const int gz = (int)(t / d.ny);
+        const int xg = gx / kGroupCells, j = gx - xg * kGroupCells;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        if (d.nzc > 0) {
+            const int zc_hi = imin(d.nzc - 1, gz / d.zchunk);
+            const int zc_lo = gz - d.zchunk - kHalo + 1 > 0 ? (int)cdiv(gz - d.zchunk - kHalo + 1, d.zchunk) : 0;
+            for (int zc = zc_lo; zc <= zc_hi; ++zc) {
+                const int pz = gz - zc * d.zchunk;
+                const int planes = imin(d.zchunk, d.ncz - zc * d.zchunk) + kHalo;
+                if (pz >= planes) continue;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int jy = gy - m;
+                    if (jy < 0 || jy >= d.ncy) continue;
+                    const long long ul = ((long long)zc * d.ncy + jy) * d.nxg + xg;
+                    const long long e = part_elem(d, ul, pz, m, j);
+                    BSI_GUARD(e >= 0 && e + 3 <= ws_floats, kErrPartRead, &g_err) {
+                        s0 += part[e];
+                        s1 += part[e + 1];
+                        s2 += part[e + 2];
+                    }
+                }
+            }
+        }
+        float* o = d.dphi + pl * 3;
+        BSI_GUARD(pl >= 0 && pl < (long long)d.nx * d.ny * d.nz, kErrDphiWrite, &g_err) {
+            o[0] = s0;
+            o[1] = s1;
+            o[2] = s2;
+        }
+    }
+}
+
+template <int MAXB, bool GENERIC>
+static cudaError_t launch_part_t(const Batch<MAXB>& b, float* part, long long ws_floats, cudaStream_t s,
+                                 LaunchInfo* info) {
+    auto kern = bsi_adjoint_partials_kernel<MAXB, GENERIC>;
+    const int wpc = warps_per_cta(b.buf_bytes);
+    const int threads = wpc * kLanes;
+    const int smem = wpc * 2 * b.buf_bytes;
+    KernelFacts f;
+    cudaError_t e = kernel_facts(reinterpret_cast<const void*>(kern), threads, smem, &f);
+    if (e != cudaSuccess) return e;
+    const long long want = cdiv(b.total_units, wpc);
+    const long long cap = (long long)f.sms * f.ctas_per_sm;
+    const int grid = (int)(want < cap ? want : cap);
+    if (info) *info = LaunchInfo{grid, threads, smem, f.ctas_per_sm};
+    if (grid <= 0) return cudaSuccess;
+    kern<<<grid, threads, smem, s>>>(b, part, ws_floats);
+    return cudaGetLastError();
+}
+
+template <int MAXB>
+cudaError_t launch_adjoint_partials(const Batch<MAXB>& b, bool generic, float* part, long long ws_floats,
+                                    cudaStream_t s, LaunchInfo* info) {
+    return generic ? launch_part_t<MAXB, true>(b, part, ws_floats, s, info)
+                   : launch_part_t<MAXB, false>(b, part, ws_floats, s, info);
+}
+
+template <int MAXB>
+cudaError_t launch_adjoint_reduce(const Batch<MAXB>& b, const float* part, long long ws_floats, cudaStream_t s,
+                                  LaunchInfo* info) {
+    auto kern = bsi_adjoint_reduce_kernel<MAXB>;
+    KernelFacts f;
+    cudaError_t e = kernel_facts(reinterpret_cast<const void*>(kern), 256, 0, &f);
+    if (e != cudaSuccess) return e;
+    const long long want = cdiv(b.total_points, 256);
+    const long long cap = (long long)f.sms * f.ctas_per_sm;
+    const int grid = (int)(want < cap ? want : cap);
+    if (info) *info = LaunchInfo{grid, 256, 0, f.ctas_per_sm};
+    if (grid <= 0) return cudaSuccess;
+    kern<<<grid, 256, 0, s>>>(b, part, ws_floats);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_adjoint_partials<1>(const Batch<1>&, bool, float*, long long, cudaStream_t, LaunchInfo*);
+template cudaError_t launch_adjoint_partials<kMaxBatch>(const Batch<kMaxBatch>&, bool, float*, long long,
+                                                         cudaStream_t, LaunchInfo*);
+template cudaError_t launch_adjoint_reduce<1>(const Batch<1>&, const float*, long long, cudaStream_t, LaunchInfo*);
+template cudaError_t launch_adjoint_reduce<kMaxBatch>(const Batch<kMaxBatch>&, const float*, long long,
+                                                       cudaStream_t, LaunchInfo*);
+
+cudaError_t adjoint_err_read_clear(unsigned* out, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_err, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_err);
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(p, 0, sizeof(unsigned), s);
+}
+
+}  // namespace bsi

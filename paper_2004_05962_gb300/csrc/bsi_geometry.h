@@ -1,0 +1,148 @@
+// bsi_geometry.h -- index arithmetic shared by the kernels and the host.
+//
+// Every global or shared-memory range a kernel touches is computed by one of
+// these functions.  They compile for the device (kernels) and for the host
+// (launch set-up and bsi_selfcheck_ranges, which walks every unit of a launch
+// on the CPU and checks each range against its buffer before anything runs).
+//
+// Work decomposition (Sec. 2.1.1: a tile is one control cell of dx*dy*dz
+// voxels, and all voxels of a tile share the same 4x4x4 control points):
+//  * a warp owns a UNIT: a strip of up to 29 x-neighbouring tiles of one
+//    tile-row (jy) and one tile-plane (kz) -- forward -- or of a chunk of
+//    tile-planes -- adjoint.  Lane l holds one column of control points, so a
+//    warp holds 32 columns and completes 32 - 3 = 29 tiles (forward) or the
+//    full sums of 29 columns (adjoint); the 3 extra lanes are the halo of the
+//    4-wide neighbourhood.
+#pragma once
+
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define BSI_HD __host__ __device__ __forceinline__
+#else
+#define BSI_HD inline
+#endif
+
+namespace bsi {
+
+constexpr int kLanes = 32;
+constexpr int kHalo = 3;                       // neighbourhood width 4 = 1 + kHalo
+constexpr int kGroupCells = kLanes - kHalo;    // tiles (forward) or columns (adjoint) per warp
+constexpr int kMaxSpacing = 64;
+constexpr int kMaxSpecializedDx = 8;           // x-spacings with a compile-time inner loop
+constexpr int kMaxBatch = 64;                  // instances per launch (kernel parameters)
+
+// One volume as the kernels see it.  Filled on the host from bsi_geom.
+struct InstDesc {
+    int X, Y, Z;
+    int dx, dy, dz;
+    int nx, ny, nz;      // stored control grid
+    int ncx, ncy, ncz;   // tiles per axis (0 for an empty volume)
+    int nxg;             // x-groups: ceil(ncx/29) forward, ceil(nx/29) adjoint
+    int nzc;             // adjoint: tile-plane chunks
+    int zchunk;          // adjoint: tile-planes per chunk
+    int reserved;
+    long long units;        // units of this instance
+    long long unit_begin;   // first global unit index of this instance in its launch
+    long long point_begin;  // adjoint reduce: first global grid point of this instance
+    long long part_off;     // adjoint: float offset of this instance's partials in the workspace
+    const float* phi;
+    void* field;
+    const float* grad;
+    float* dphi;
+};
+
+template <int MAXB>
+struct Batch {
+    int n;
+    int buf_bytes;          // bytes of ONE per-warp staging buffer (two per warp)
+    long long total_units;
+    long long total_points;
+    InstDesc inst[MAXB];
+};
+
+BSI_HD long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
+BSI_HD int imin(int a, int b) { return a < b ? a : b; }
+BSI_HD int imax(int a, int b) { return a > b ? a : b; }
+
+// Offset of the 4*d weights of spacing d in the weight table: sum_{e<d} 4e.
+BSI_HD constexpr int weight_base(int d) { return 2 * d * (d - 1); }
+constexpr int kWeightCount = weight_base(kMaxSpacing + 1);
+
+// Element (float or bf16) offset of voxel (x, y, z) channel 0 in a field.
+BSI_HD long long field_elem(const InstDesc& d, int z, int y, int x) {
+    return (((long long)z * d.Y + y) * d.X + x) * 3;
+}
+
+// Float offset of stored control point (gx, gy, gz) channel 0.
+BSI_HD long long phi_elem(const InstDesc& d, int gz, int gy, int gx) {
+    return (((long long)gz * d.ny + gy) * d.nx + gx) * 3;
+}
+
+// ---------------------------------------------------------------- forward
+
+struct FwdUnit {
+    int kz, jy, xg;
+    int cell0;   // first tile of the strip; lane l holds grid column cell0 + l
+    int ncell;   // tiles the warp outputs (<= 29)
+    int x0;      // first voxel of the strip
+    int nvox;    // voxels per row of the strip
+};
+
+BSI_HD FwdUnit fwd_unit(const InstDesc& d, long long ul) {
+    FwdUnit u;
+    u.xg = (int)(ul % d.nxg);
+    const long long t = ul / d.nxg;
+    u.jy = (int)(t % d.ncy);
+    u.kz = (int)(t / d.ncy);
+    u.cell0 = u.xg * kGroupCells;
+    u.ncell = imin(kGroupCells, d.ncx - u.cell0);
+    u.x0 = u.cell0 * d.dx;
+    u.nvox = imin(u.ncell * d.dx, d.X - u.x0);
+    return u;
+}
+
+// ---------------------------------------------------------------- adjoint
+
+struct AdjUnit {
+    int zc, jy, xg;
+    int col0;    // first complete column; lane l holds tile / column col0 - 3 + l
+    int xs;      // first voxel read by the warp
+    int nvox;    // voxels per row read by the warp
+    int kz0, kz1;
+};
+
+BSI_HD AdjUnit adj_unit(const InstDesc& d, long long ul) {
+    AdjUnit u;
+    u.xg = (int)(ul % d.nxg);
+    const long long t = ul / d.nxg;
+    u.jy = (int)(t % d.ncy);
+    u.zc = (int)(t / d.ncy);
+    u.col0 = u.xg * kGroupCells;
+    const int c_lo = imax(0, u.col0 - kHalo);
+    const int c_hi = imin(d.ncx, u.col0 + kGroupCells);
+    u.xs = c_lo * d.dx;
+    u.nvox = c_hi > c_lo ? imin(d.X, c_hi * d.dx) - u.xs : 0;
+    u.kz0 = u.zc * d.zchunk;
+    u.kz1 = imin(d.ncz, u.kz0 + d.zchunk);
+    return u;
+}
+
+// Floats of partial sums one adjoint unit writes: (zchunk + 3) planes x 4 rows
+// x 29 columns x 3 channels.
+BSI_HD long long adj_unit_floats(const InstDesc& d) {
+    return (long long)(d.zchunk + kHalo) * 4 * kGroupCells * 3;
+}
+
+BSI_HD long long part_elem(const InstDesc& d, long long ul, int pz, int m, int j) {
+    return d.part_off + ul * adj_unit_floats(d) + (((long long)pz * 4 + m) * kGroupCells + j) * 3;
+}
+
+// Staging buffer bytes for a largest x-spacing dxmax: one row segment of up to
+// 32 tiles x dxmax voxels x 3 FP32 channels, plus up to 15 bytes of alignment shift.
+BSI_HD int stage_buf_bytes(int dxmax) {
+    const int b = 16 + kLanes * dxmax * 3 * 4;
+    return (b + 15) & ~15;
+}
+
+}  // namespace bsi

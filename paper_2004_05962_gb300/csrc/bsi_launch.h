@@ -1,0 +1,48 @@
+// bsi_launch.h -- host-side launchers shared by the C ABI (bsi_abi.cu) and the
+// kernel translation units (bsi_forward.cu, bsi_adjoint.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "bsi_geometry.h"
+
+namespace bsi {
+
+// What a launcher chose; returned for diagnostics and the self-check.
+struct LaunchInfo {
+    int grid = 0;
+    int block = 0;
+    int smem = 0;
+    int ctas_per_sm = 0;
+};
+
+template <int MAXB>
+cudaError_t launch_forward(const Batch<MAXB>& b, bool bf16, bool generic, cudaStream_t s,
+                           LaunchInfo* info);
+
+template <int MAXB>
+cudaError_t launch_adjoint_partials(const Batch<MAXB>& b, bool generic, float* part,
+                                    long long ws_floats, cudaStream_t s, LaunchInfo* info);
+
+template <int MAXB>
+cudaError_t launch_adjoint_reduce(const Batch<MAXB>& b, const float* part, long long ws_floats,
+                                  cudaStream_t s, LaunchInfo* info);
+
+// Reads and clears the kernel error word of each translation unit (enqueued
+// on s; the caller synchronises before looking at *out).
+cudaError_t forward_err_read_clear(unsigned* out, cudaStream_t s);
+cudaError_t adjoint_err_read_clear(unsigned* out, cudaStream_t s);
+
+// Per-device, per-kernel launch facts, computed once (outside any capture the
+// first call per device does this host-side work; no stream work is issued).
+struct KernelFacts {
+    int sms = 0;
+    int ctas_per_sm = 0;
+};
+
+// Looks up (and on first use per device computes) the SM count and the
+// resident CTAs per SM of `kernel` at `threads` x `smem`.  Raises the dynamic
+// shared-memory limit of the kernel when smem exceeds 48 KB.
+cudaError_t kernel_facts(const void* kernel, int threads, int smem, KernelFacts* out);
+
+}  // namespace bsi

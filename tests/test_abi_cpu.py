@@ -1,0 +1,195 @@
+"""The C-ABI library on the CPU: it loads, exports every symbol include/bsi.h
+declares, rejects bad arguments before touching CUDA, and every planned
+kernel access lies inside its buffer (host-only range self-check)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2004_05962_gb300 as P
+from paper_2004_05962_gb300 import bsi as B
+from paper_2004_05962_gb300 import build as Bd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    Bd.build()
+    return B.library()
+
+
+def header_symbols():
+    src = open(os.path.join(ROOT, "include", "bsi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bsi_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_what_binding_binds():
+    assert header_symbols() == sorted(B.exported_symbols())
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_symbols():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_status_strings(lib):
+    for code, name in B.STATUS.items():
+        assert lib.bsi_status_string(code).decode().startswith(name)
+    assert lib.bsi_version() >= 100
+
+
+def _geom(X, Y, Z, dx, dy, dz):
+    g = B.BsiGeom()
+    st = B.library().bsi_geom_init(ctypes.byref(g), X, Y, Z, dx, dy, dz)
+    return g, st
+
+
+def test_geom_init_and_limits(lib):
+    g, st = _geom(64, 64, 64, 5, 5, 5)
+    assert st == 0 and (g.nx, g.ny, g.nz) == (16, 16, 16)
+    g, st = _geom(512, 512, 300, 5, 5, 5)
+    assert (g.nx, g.ny, g.nz) == (106, 106, 63)
+    assert _geom(-1, 4, 4, 2, 2, 2)[1] == 2
+    assert _geom(4, 4, (1 << 20) + 1, 2, 2, 2)[1] == 2
+    assert _geom(4, 4, 4, 0, 2, 2)[1] == 3
+    assert _geom(4, 4, 4, 2, 65, 2)[1] == 3
+    assert lib.bsi_geom_init(None, 4, 4, 4, 1, 1, 1) == 1
+    g, st = _geom(0, 7, 7, 3, 3, 3)
+    assert st == 0 and g.nx == 3
+
+
+FAKE_DEV = 0x7F0000000000  # never dereferenced: every call below fails validation first
+
+
+def test_forward_validation_before_cuda(lib):
+    g, _ = _geom(10, 10, 10, 3, 3, 3)
+    assert lib.bsi_field_forward(None, FAKE_DEV, FAKE_DEV, 0, None) == 1
+    assert lib.bsi_field_forward(ctypes.byref(g), None, FAKE_DEV, 0, None) == 1
+    assert lib.bsi_field_forward(ctypes.byref(g), FAKE_DEV, None, 0, None) == 1
+    assert lib.bsi_field_forward(ctypes.byref(g), FAKE_DEV, FAKE_DEV, 7, None) == 5
+    assert lib.bsi_field_forward(ctypes.byref(g), FAKE_DEV + 2, FAKE_DEV, 0, None) == 6
+    assert lib.bsi_field_forward(ctypes.byref(g), FAKE_DEV, FAKE_DEV + 2, 0, None) == 6
+    assert lib.bsi_field_forward(ctypes.byref(g), FAKE_DEV, FAKE_DEV + 1, 1, None) == 6
+    bad = B.BsiGeom.from_buffer_copy(g)
+    bad.nx += 1
+    assert lib.bsi_field_forward(ctypes.byref(bad), FAKE_DEV, FAKE_DEV, 0, None) == 4
+    bad = B.BsiGeom.from_buffer_copy(g)
+    bad.dy = 0
+    assert lib.bsi_field_forward(ctypes.byref(bad), FAKE_DEV, FAKE_DEV, 0, None) == 3
+
+
+def test_adjoint_validation_before_cuda(lib):
+    g, _ = _geom(40, 30, 20, 5, 4, 3)
+    need = lib.bsi_adjoint_workspace_bytes(ctypes.byref(g))
+    assert need > 0 and need % 16 == 0
+    assert lib.bsi_field_adjoint(ctypes.byref(g), FAKE_DEV, FAKE_DEV, FAKE_DEV, need - 4, None) == 7
+    assert lib.bsi_field_adjoint(ctypes.byref(g), FAKE_DEV, FAKE_DEV, None, need, None) == 7
+    assert lib.bsi_field_adjoint(ctypes.byref(g), FAKE_DEV, FAKE_DEV, FAKE_DEV + 4, need, None) == 6
+    assert lib.bsi_field_adjoint(ctypes.byref(g), None, FAKE_DEV, FAKE_DEV, need, None) == 1
+    assert lib.bsi_field_adjoint(ctypes.byref(g), FAKE_DEV, None, FAKE_DEV, need, None) == 1
+    e, _ = _geom(0, 30, 20, 5, 4, 3)
+    assert lib.bsi_adjoint_workspace_bytes(ctypes.byref(e)) == 0
+
+
+def test_batched_validation_before_cuda(lib):
+    assert lib.bsi_field_forward_batched(None, 3, 0, None) == 10
+    assert lib.bsi_field_forward_batched(None, -1, 0, None) == 10
+    arr = (B.BsiInstance * 2)()
+    g, _ = _geom(10, 10, 10, 3, 3, 3)
+    arr[0].geom = g
+    arr[1].geom = g
+    arr[0].phi = arr[0].field = arr[1].phi = FAKE_DEV
+    assert lib.bsi_field_forward_batched(arr, 2, 0, None) == 1  # arr[1].field is NULL
+    arr[1].field = FAKE_DEV
+    arr[1].geom.nz = 99
+    assert lib.bsi_field_forward_batched(arr, 2, 0, None) == 4
+    assert lib.bsi_batched_adjoint_workspace_bytes(arr, 2) == 0  # invalid geometry -> 0
+
+
+def test_no_gpu_means_cuda_error_not_fallback(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    g, _ = _geom(10, 10, 10, 3, 3, 3)
+    st = lib.bsi_field_forward(ctypes.byref(g), FAKE_DEV, FAKE_DEV, 0, None)
+    assert st == 8
+    assert lib.bsi_last_cuda_error().decode()
+
+
+def test_binding_fails_loudly_when_library_missing(monkeypatch, tmp_path):
+    monkeypatch.setattr(B, "_LIBS", {})
+    monkeypatch.setattr(Bd, "BUILD", tmp_path)
+    with pytest.raises(B.BsiLibraryMissing):
+        B.library()
+
+
+# ------------------------------------------------------------ range self-check
+
+EDGE_CASES = [
+    ((64, 64, 64), (5, 5, 5)),
+    ((1, 1, 1), (1, 1, 1)),
+    ((1, 1, 1), (64, 64, 64)),
+    ((3, 5, 7), (1, 2, 3)),
+    ((17, 1, 33), (4, 1, 8)),
+    ((9, 13, 300), (2, 3, 9)),       # generic x-spacing, long row
+    ((5, 6, 1000), (3, 3, 7)),       # several x-groups
+    ((7, 11, 29 * 8 + 1), (2, 2, 8)),  # ragged last x-group
+    ((4, 4, 87), (3, 3, 3)),         # exactly 29 tiles per row
+    ((30, 20, 130), (6, 5, 64)),     # spacing 64
+    ((12, 40, 60), (16, 4, 13)),
+    ((0, 10, 10), (3, 3, 3)),
+    ((10, 0, 10), (3, 3, 3)),
+    ((10, 10, 0), (3, 3, 3)),
+]
+
+
+@pytest.mark.parametrize("op", ["forward", "forward_bf16", "adjoint"])
+def test_selfcheck_edge_cases(lib, op):
+    for shape, spacing in EDGE_CASES:
+        n, msg = P.bsi_selfcheck_ranges([shape], [spacing], op, cover=True)
+        assert n == 0, (shape, spacing, msg)
+
+
+@pytest.mark.parametrize("op", ["forward", "adjoint"])
+def test_selfcheck_random_geometries(lib, op):
+    rng = np.random.default_rng(7)
+    for _ in range(60):
+        shape = tuple(int(v) for v in rng.integers(1, 90, 3))
+        spacing = tuple(int(v) for v in rng.integers(1, 12, 3))
+        n, msg = P.bsi_selfcheck_ranges([shape], [spacing], op, cover=True)
+        assert n == 0, (shape, spacing, msg)
+
+
+@pytest.mark.parametrize("op", ["forward", "adjoint"])
+def test_selfcheck_batches(lib, op):
+    from paper_2004_05962_gb300 import synth
+
+    geoms = synth.batch_geometries(64, seed=5)
+    geoms += [((20, 30, 40), (3, 4, 11)), ((0, 3, 3), (2, 2, 2)), ((5, 5, 5), (9, 9, 9))]
+    geoms += synth.batch_geometries(70, seed=9, xy_range=(8, 40), z_range=(8, 30), spacing_range=(1, 10))
+    n, msg = P.bsi_selfcheck_ranges([g[0] for g in geoms], [g[1] for g in geoms], op, cover=True)
+    assert n == 0, msg
+
+
+@pytest.mark.parametrize("spacing", [(3, 3, 3), (5, 5, 5), (6, 5, 4), (8, 8, 8)])
+def test_selfcheck_full_size_volumes(lib, spacing):
+    for op in ("forward", "adjoint"):
+        n, msg = P.bsi_selfcheck_ranges([(512, 512, 512)], [spacing], op, cover=False)
+        assert n == 0, msg
+    n, msg = P.bsi_selfcheck_ranges([(300, 512, 512)], [(5, 5, 5)], "forward_bf16", cover=False)
+    assert n == 0, msg
+
+
+def test_selfcheck_detects_a_bad_plan(lib):
+    """The checker itself is not vacuous: an invalid geometry is reported."""
+    arr = (B.BsiInstance * 1)()
+    g, _ = _geom(10, 10, 10, 3, 3, 3)
+    g.nx = 2
+    arr[0].geom = g
+    buf = ctypes.create_string_buffer(256)
+    assert lib.bsi_selfcheck_ranges(arr, 1, 0, 1, buf, 256) > 0
