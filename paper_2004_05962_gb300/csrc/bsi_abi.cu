@@ -33,10 +33,14 @@ cudaError_t kernel_facts(const void* kernel, int threads, int smem, KernelFacts*
         }
     };
     static std::unordered_map<Key, KernelFacts, KeyHash> cache;
+    // The dynamic shared-memory limit is an attribute of the kernel, not of a
+    // launch: it is only ever raised, to the largest size requested so far.
+    static std::unordered_map<Key, int, KeyHash> smem_limit;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const Key key{kernel, dev, threads, smem};
+    const Key kkey{kernel, dev, 0, 0};
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
     if (it != cache.end()) {
@@ -46,9 +50,12 @@ cudaError_t kernel_facts(const void* kernel, int threads, int smem, KernelFacts*
     KernelFacts f;
     e = cudaDeviceGetAttribute(&f.sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    if (smem > 48 * 1024) {
+    auto lim = smem_limit.find(kkey);
+    const int have = lim == smem_limit.end() ? 48 * 1024 : lim->second;
+    if (smem > have) {
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
+        smem_limit[kkey] = smem;
     }
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&f.ctas_per_sm, kernel, threads, (size_t)smem);
     if (e != cudaSuccess) return e;
@@ -177,6 +184,7 @@ enum class Op { Forward, AdjointPartials, AdjointReduce };
 
 static cudaError_t run_group(const Group& g, Op op, bool bf16, float* part, long long ws_floats,
                              cudaStream_t s) {
+    (void)cudaGetLastError();  // a launch must not report an earlier call's returned error
     if (g.inst.size() == 1) {
         Batch<1> b;
         to_batch(g, b);
