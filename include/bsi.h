@@ -63,7 +63,8 @@ typedef enum {
     BSI_ERR_WORKSPACE = 7,     /* workspace NULL or smaller than required */
     BSI_ERR_CUDA = 8,          /* a CUDA runtime call failed */
     BSI_ERR_DEVICE_STATUS = 9, /* a kernel recorded an error (bsi_check_device_status) */
-    BSI_ERR_BATCH = 10         /* n < 0, or instances == NULL with n > 0 */
+    BSI_ERR_BATCH = 10,        /* n < 0, or instances == NULL with n > 0 */
+    BSI_ERR_SCRATCH_LIMIT = 11 /* volume needs more than BSI_NOALLOC_SCRATCH_BYTES of scratch */
 } bsi_status;
 
 typedef enum { BSI_F32 = 0, BSI_BF16 = 1 } bsi_dtype;
@@ -135,6 +136,32 @@ size_t bsi_batched_adjoint_workspace_bytes(const bsi_instance* inst, int n);
  * overwritten. */
 bsi_status bsi_field_adjoint_batched(const bsi_instance* inst, int n, void* workspace,
                                      size_t workspace_bytes, bsi_stream_t stream);
+
+/* Adjoint without caller-provided scratch, for callers that cannot allocate
+ * device memory: code running while a stream is being captured into a CUDA
+ * graph (where cudaMalloc is not allowed), plug-ins that live inside a host
+ * application which owns every device allocation through its own pool, and
+ * plain C callers that have device buffers for their data but no allocator
+ * for temporaries.  The paper has no counterpart; it is an operational
+ * variant of bsi_field_adjoint, whose arguments and result it shares.
+ *
+ * Scratch: a file-scope device array of BSI_NOALLOC_SCRATCH_BYTES (64 MiB)
+ * inside the library, held on every device where the library's module is
+ * loaded until the process exits.  Volumes whose bsi_adjoint_workspace_bytes
+ * exceed it are rejected with BSI_ERR_SCRATCH_LIMIT before anything is
+ * enqueued (the 512x512x300 volume at spacing 5 needs about 60 MB).
+ * The call allocates no device memory: no cudaMalloc, cudaFree or allocating
+ * library routine.  Its first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, once per device, with that device current),
+ * so make that first call before any stream capture.
+ * Every call uses the same array, which keeps the previous call's contents;
+ * the first kernel writes every scratch entry the second one reads, so no
+ * clearing is needed.  Calls that overlap on the GPU (different streams, or
+ * other threads, without ordering between them) race on the array: order
+ * them on one stream or synchronise between them. */
+#define BSI_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+bsi_status bsi_field_adjoint_noalloc(const bsi_geom* g, const float* grad_field, float* grad_phi,
+                                     bsi_stream_t stream);
 
 /* Static string naming a status code. */
 const char* bsi_status_string(bsi_status s);

@@ -24,7 +24,7 @@ BSI_F32, BSI_BF16 = 0, 1
 STATUS = {
     0: "BSI_OK", 1: "BSI_ERR_NULL", 2: "BSI_ERR_DIMS", 3: "BSI_ERR_SPACING",
     4: "BSI_ERR_GRID_MISMATCH", 5: "BSI_ERR_DTYPE", 6: "BSI_ERR_ALIGN", 7: "BSI_ERR_WORKSPACE",
-    8: "BSI_ERR_CUDA", 9: "BSI_ERR_DEVICE_STATUS", 10: "BSI_ERR_BATCH",
+    8: "BSI_ERR_CUDA", 9: "BSI_ERR_DEVICE_STATUS", 10: "BSI_ERR_BATCH", 11: "BSI_ERR_SCRATCH_LIMIT",
 }
 
 
@@ -95,6 +95,7 @@ def library(checked: bool | None = None) -> ctypes.CDLL:
         "bsi_check_device_status": (i32, [vp, ctypes.POINTER(ctypes.c_uint32)]),
         "bsi_version": (i32, []),
         "bsi_selfcheck_ranges": (i32, [I, i32, i32, i32, ctypes.c_char_p, sz]),
+        "bsi_field_adjoint_noalloc": (i32, [G, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -108,7 +109,8 @@ def exported_symbols():
     return ["bsi_geom_init", "bsi_field_forward", "bsi_adjoint_workspace_bytes", "bsi_field_adjoint",
             "bsi_field_forward_batched", "bsi_batched_adjoint_workspace_bytes",
             "bsi_field_adjoint_batched", "bsi_status_string", "bsi_last_cuda_error",
-            "bsi_check_device_status", "bsi_version", "bsi_selfcheck_ranges"]
+            "bsi_check_device_status", "bsi_version", "bsi_selfcheck_ranges",
+            "bsi_field_adjoint_noalloc"]
 
 
 # ---------------------------------------------------------------- helpers
@@ -211,6 +213,25 @@ def bsi_field_adjoint(grad_field, spacing, out=None, workspace=None, stream=None
                                      ws.data_ptr() if ws is not None else None, wsb,
                                      _stream(stream, grad_field.device))
     _check(st, "bsi_field_adjoint")
+    return out
+
+
+def bsi_field_adjoint_noalloc(grad_field, spacing, out=None, stream=None):
+    """``bsi_field_adjoint`` without a workspace argument: the partial sums go to
+    a fixed 64 MiB device array inside the library, for callers that cannot
+    allocate device memory.  Calls that overlap on the GPU race on that array."""
+    _need(grad_field, "grad_field", torch.float32)
+    if grad_field.dim() != 4 or grad_field.shape[3] != 3:
+        raise ValueError("grad_field must be [Z, Y, X, 3]")
+    shape = tuple(grad_field.shape[:3])
+    grid = grid_shape(shape, spacing)
+    if out is None:
+        out = torch.empty(grid + (3,), dtype=torch.float32, device=grad_field.device)
+    _need(out, "out", torch.float32, grid + (3,))
+    g = make_geom(shape, spacing)
+    st = library().bsi_field_adjoint_noalloc(ctypes.byref(g), grad_field.data_ptr(), out.data_ptr(),
+                                             _stream(stream, grad_field.device))
+    _check(st, "bsi_field_adjoint_noalloc")
     return out
 
 

@@ -467,6 +467,7 @@ const char* bsi_status_string(bsi_status s) {
         case BSI_ERR_CUDA: return "BSI_ERR_CUDA: a CUDA call failed";
         case BSI_ERR_DEVICE_STATUS: return "BSI_ERR_DEVICE_STATUS: a kernel recorded an error";
         case BSI_ERR_BATCH: return "BSI_ERR_BATCH: bad instance count or list";
+        case BSI_ERR_SCRATCH_LIMIT: return "BSI_ERR_SCRATCH_LIMIT: volume needs more than the built-in 64 MiB scratch";
     }
     return "unknown bsi_status";
 }
@@ -521,3 +522,60 @@ int bsi_selfcheck_ranges(const bsi_instance* inst, int n, int op, int cover, cha
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------- adjoint without caller scratch
+//
+// For callers that cannot allocate device memory (stream capture in progress,
+// host applications that own all device allocations, plain C callers without a
+// device allocator): the partial sums of bsi_field_adjoint live in a fixed
+// array inside the library instead of a caller workspace.
+
+namespace bsi {
+
+constexpr size_t kNoAllocScratchBytes = BSI_NOALLOC_SCRATCH_BYTES;
+
+// In host code this name is only a handle for the runtime; kernels get the
+// device address that noalloc_scratch() looks up.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch on the current device, looked up once per
+// device (with that device current) and cached.
+static cudaError_t noalloc_scratch(void** out) {
+    static std::mutex mu;
+    static std::unordered_map<int, void*> addr;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = addr.find(dev);
+    if (it == addr.end()) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        it = addr.emplace(dev, p).first;
+    }
+    *out = it->second;
+    return cudaSuccess;
+}
+
+}  // namespace bsi
+
+extern "C" bsi_status bsi_field_adjoint_noalloc(const bsi_geom* g, const float* grad_field, float* grad_phi,
+                                                bsi_stream_t stream) {
+    if (!g) return BSI_ERR_NULL;
+    bsi_instance in;
+    std::memset(&in, 0, sizeof in);
+    in.geom = *g;
+    in.grad_field = grad_field;
+    in.grad_phi = grad_phi;
+    const bsi_status st = check_instances(&in, 1, false, true, BSI_F32);
+    if (st != BSI_OK) return st;
+    const size_t need = bsi_adjoint_workspace_bytes(g);
+    if (need > kNoAllocScratchBytes) return BSI_ERR_SCRATCH_LIMIT;
+    void* scratch = nullptr;
+    if (need > 0) {
+        const cudaError_t e = noalloc_scratch(&scratch);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return adjoint_impl(&in, 1, scratch, kNoAllocScratchBytes, reinterpret_cast<cudaStream_t>(stream));
+}
