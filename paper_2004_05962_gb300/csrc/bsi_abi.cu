@@ -302,6 +302,8 @@ static void check_forward_group(const Group& g, int es, RangeChecker& rc, bool c
             const int z0 = u.kz * d.dz, zn = imin(d.dz, d.Z - z0);
             const int y0 = u.jy * d.dy, yn = imin(d.dy, d.Y - y0);
             if (15 + u.nvox * 3 * es > buf) rc.fail("staging overflow", u.nvox, buf);
+            if (warps_per_cta(fwd_warp_smem(buf)) * fwd_warp_smem(buf) > kSmemBudget)
+                rc.fail("forward shared memory over budget", buf, kSmemBudget);
             for (int rz = 0; rz < zn; ++rz)
                 for (int ry = 0; ry < yn; ++ry) {
                     const long long e0 = field_elem(d, z0 + rz, y0 + ry, u.x0);
@@ -327,7 +329,10 @@ static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecke
         for (long long ul = 0; ul < d.units; ++ul) {
             const AdjUnit u = adj_unit(d, ul);
             if (u.kz1 <= u.kz0) rc.fail("adjoint unit without planes", ul, u.kz0);
-            if (15 + u.nvox * 12 > buf) rc.fail("staging overflow", u.nvox, buf);
+            // a bulk load covers the 16-byte-aligned superset of the row: <= nbytes + 30
+            if (30 + u.nvox * 12 > buf) rc.fail("staging overflow", u.nvox, buf);
+            if (warps_per_cta(adj_warp_smem(buf)) * adj_warp_smem(buf) > kSmemBudget)
+                rc.fail("adjoint shared memory over budget", buf, kSmemBudget);
             for (int lane = 0; lane < kLanes; ++lane) {
                 const int cell = u.col0 - kHalo + lane;
                 const int nv = (cell >= 0 && cell < d.ncx) ? imin(d.dx, d.X - cell * d.dx) : 0;

@@ -10,39 +10,51 @@
 
 namespace bsi {
 
-static __constant__ WeightTable c_lut = make_weight_table();
 static __device__ unsigned g_err;
 
 template <int MAXB, bool GENERIC>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
     bsi_adjoint_partials_kernel(const __grid_constant__ Batch<MAXB> b, float* __restrict__ part,
                                 long long ws_floats) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & (kLanes - 1);
     const int warp = threadIdx.x >> 5;
-    unsigned char* stage = smem + (size_t)warp * 2 * b.buf_bytes;
+    unsigned char* wsm = smem + (size_t)warp * adj_warp_smem(b.buf_bytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm);           // mbarrier of stage s: bars[s]
+    unsigned char* bufs = wsm + 16 * kLoadStages;                 // kLoadStages ring buffers
+    if (lane == 0) {
+        for (int s = 0; s < kLoadStages; ++s) mbar_init(bars + s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
     const int wpc = blockDim.x >> 5;
     const long long nwarps = (long long)gridDim.x * wpc;
-    int ii = 0, par = 0;
+    int ii = 0;
+    unsigned q = 0;
     for (long long uu = (long long)blockIdx.x * wpc + warp; uu < b.total_units; uu += nwarps) {
         while (ii + 1 < b.n && uu >= b.inst[ii + 1].unit_begin) ++ii;
         const InstDesc& d = b.inst[ii];
         const long long ul = uu - d.unit_begin;
+        bool ok;
         if (GENERIC) {
-            adjoint_unit<0>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err);
+            ok = adjoint_unit<0>(d, ul, bars, bufs, b.buf_bytes, lane, q, part, ws_floats, &g_err);
         } else {
             switch (d.dx) {
-                case 1: adjoint_unit<1>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
-                case 2: adjoint_unit<2>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
-                case 3: adjoint_unit<3>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
-                case 4: adjoint_unit<4>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
-                case 5: adjoint_unit<5>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
-                case 6: adjoint_unit<6>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
-                case 7: adjoint_unit<7>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
-                default: adjoint_unit<8>(c_lut, d, ul, stage, b.buf_bytes, lane, par, part, ws_floats, &g_err); break;
+                case 1: ok = adjoint_unit<1>(d, ul, bars, bufs, b.buf_bytes, lane, q, part, ws_floats, &g_err); break;
+                case 2: ok = adjoint_unit<2>(d, ul, bars, bufs, b.buf_bytes, lane, q, part, ws_floats, &g_err); break;
+                case 3: ok = adjoint_unit<3>(d, ul, bars, bufs, b.buf_bytes, lane, q, part, ws_floats, &g_err); break;
+                case 4: ok = adjoint_unit<4>(d, ul, bars, bufs, b.buf_bytes, lane, q, part, ws_floats, &g_err); break;
+                case 5: ok = adjoint_unit<5>(d, ul, bars, bufs, b.buf_bytes, lane, q, part, ws_floats, &g_err); break;
+                case 6: ok = adjoint_unit<6>(d, ul, bars, bufs, b.buf_bytes, lane, q, part, ws_floats, &g_err); break;
+                case 7: ok = adjoint_unit<7>(d, ul, bars, bufs, b.buf_bytes, lane, q, part, ws_floats, &g_err); break;
+                default: ok = adjoint_unit<8>(d, ul, bars, bufs, b.buf_bytes, lane, q, part, ws_floats, &g_err); break;
             }
         }
+        if (!ok) break;  // a lost bulk copy: the error word says so; stop this warp
     }
+    __syncwarp();
+    if (lane == 0)
+        for (int s = 0; s < kLoadStages; ++s) mbar_inval(bars + s);
 }
 
 // One thread per stored control point of every instance.  The units that
@@ -103,9 +115,9 @@ template <int MAXB, bool GENERIC>
 static cudaError_t launch_part_t(const Batch<MAXB>& b, float* part, long long ws_floats, cudaStream_t s,
                                  LaunchInfo* info) {
     auto kern = bsi_adjoint_partials_kernel<MAXB, GENERIC>;
-    const int wpc = warps_per_cta(b.buf_bytes);
+    const int wpc = warps_per_cta(adj_warp_smem(b.buf_bytes));
     const int threads = wpc * kLanes;
-    const int smem = wpc * 2 * b.buf_bytes;
+    const int smem = wpc * adj_warp_smem(b.buf_bytes);
     KernelFacts f;
     cudaError_t e = kernel_facts(reinterpret_cast<const void*>(kern), threads, smem, &f);
     if (e != cudaSuccess) return e;

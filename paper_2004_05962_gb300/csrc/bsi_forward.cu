@@ -4,7 +4,6 @@
 
 namespace bsi {
 
-static __constant__ WeightTable c_lut = make_weight_table();
 static __device__ unsigned g_err;
 
 // Persistent grid: warp w of the launch takes units w, w + W, w + 2W, ... of
@@ -12,41 +11,46 @@ static __device__ unsigned g_err;
 // per-unit work is near-uniform, so the static stride balances without an
 // atomic ticket and is deterministic.
 template <int MAXB, bool BF16, bool GENERIC>
-__global__ void __launch_bounds__(kThreads, 2) bsi_forward_kernel(const __grid_constant__ Batch<MAXB> b) {
+__global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
+    bsi_forward_kernel(const __grid_constant__ Batch<MAXB> b) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & (kLanes - 1);
     const int warp = threadIdx.x >> 5;
-    unsigned char* stage = smem + (size_t)warp * 2 * b.buf_bytes;
+    unsigned char* stage = smem + (size_t)warp * fwd_warp_smem(b.buf_bytes);
     const int wpc = blockDim.x >> 5;
     const long long nwarps = (long long)gridDim.x * wpc;
-    int ii = 0, par = 0;
+    int ii = 0;
+    unsigned rowc = 0;
     for (long long uu = (long long)blockIdx.x * wpc + warp; uu < b.total_units; uu += nwarps) {
         while (ii + 1 < b.n && uu >= b.inst[ii + 1].unit_begin) ++ii;
         const InstDesc& d = b.inst[ii];
         const long long ul = uu - d.unit_begin;
         if (GENERIC) {
-            forward_unit<0, BF16>(c_lut, d, ul, stage, b.buf_bytes, lane, par, &g_err);
+            forward_unit<0, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err);
         } else {
             switch (d.dx) {
-                case 1: forward_unit<1, BF16>(c_lut, d, ul, stage, b.buf_bytes, lane, par, &g_err); break;
-                case 2: forward_unit<2, BF16>(c_lut, d, ul, stage, b.buf_bytes, lane, par, &g_err); break;
-                case 3: forward_unit<3, BF16>(c_lut, d, ul, stage, b.buf_bytes, lane, par, &g_err); break;
-                case 4: forward_unit<4, BF16>(c_lut, d, ul, stage, b.buf_bytes, lane, par, &g_err); break;
-                case 5: forward_unit<5, BF16>(c_lut, d, ul, stage, b.buf_bytes, lane, par, &g_err); break;
-                case 6: forward_unit<6, BF16>(c_lut, d, ul, stage, b.buf_bytes, lane, par, &g_err); break;
-                case 7: forward_unit<7, BF16>(c_lut, d, ul, stage, b.buf_bytes, lane, par, &g_err); break;
-                default: forward_unit<8, BF16>(c_lut, d, ul, stage, b.buf_bytes, lane, par, &g_err); break;
+                case 1: forward_unit<1, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
+                case 2: forward_unit<2, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
+                case 3: forward_unit<3, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
+                case 4: forward_unit<4, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
+                case 5: forward_unit<5, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
+                case 6: forward_unit<6, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
+                case 7: forward_unit<7, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
+                default: forward_unit<8, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
             }
         }
     }
+    // the staging ring must outlive every bulk copy that reads it
+    if (lane == 0) bulk_wait_all<0>();
+    __syncwarp();
 }
 
 template <int MAXB, bool BF16, bool GENERIC>
 static cudaError_t launch_fwd_t(const Batch<MAXB>& b, cudaStream_t s, LaunchInfo* info) {
     auto kern = bsi_forward_kernel<MAXB, BF16, GENERIC>;
-    const int wpc = warps_per_cta(b.buf_bytes);
+    const int wpc = warps_per_cta(fwd_warp_smem(b.buf_bytes));
     const int threads = wpc * kLanes;
-    const int smem = wpc * 2 * b.buf_bytes;
+    const int smem = wpc * fwd_warp_smem(b.buf_bytes);
     KernelFacts f;
     cudaError_t e = kernel_facts(reinterpret_cast<const void*>(kern), threads, smem, &f);
     if (e != cudaSuccess) return e;

@@ -139,10 +139,29 @@ BSI_HD long long part_elem(const InstDesc& d, long long ul, int pz, int m, int j
 }
 
 // Staging buffer bytes for a largest x-spacing dxmax: one row segment of up to
-// 32 tiles x dxmax voxels x 3 FP32 channels, plus up to 15 bytes of alignment shift.
+// 32 tiles x dxmax voxels x 3 FP32 channels, plus up to 15 bytes of alignment
+// shift on each side (the adjoint's bulk loads cover the 16-byte-aligned
+// superset of a row segment).
 BSI_HD int stage_buf_bytes(int dxmax) {
-    const int b = 16 + kLanes * dxmax * 3 * 4;
+    const int b = 32 + kLanes * dxmax * 3 * 4;
     return (b + 15) & ~15;
+}
+
+constexpr int kStoreStages = 3;   // forward: ring of staging buffers per warp (bulk stores in flight)
+constexpr int kLoadStages = 4;    // adjoint: ring of staging buffers per warp (bulk loads in flight)
+
+// Shared memory of one warp: forward -- the store ring; adjoint -- one 16-byte
+// mbarrier slot per stage, then the load ring.
+BSI_HD int fwd_warp_smem(int buf_bytes) { return kStoreStages * buf_bytes; }
+BSI_HD int adj_warp_smem(int buf_bytes) { return kLoadStages * (16 + buf_bytes); }
+
+constexpr int kMaxWarpsPerCta = 8;
+constexpr int kSmemBudget = 200 * 1024;   // dynamic shared memory per CTA we allow
+
+// Warps per CTA such that the warps' shared memory fits the budget.
+BSI_HD int warps_per_cta(int warp_smem) {
+    const int w = kSmemBudget / warp_smem;
+    return w < 1 ? 1 : (w > kMaxWarpsPerCta ? kMaxWarpsPerCta : w);
 }
 
 }  // namespace bsi

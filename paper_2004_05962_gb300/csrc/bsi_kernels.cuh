@@ -10,39 +10,36 @@
 // column of control displacements at grid column cell0 + l in registers (the
 // register reuse of Sec. 3.2.2, one column per lane instead of one 4x4x4 cube
 // per thread), contracts it along z and y, and takes the three x-neighbour
-// columns from lanes l+1..l+3 with shuffles.  Rows are staged in a per-warp
-// shared-memory buffer and written with 16-byte coalesced stores -- the paper
-// found its one-thread-per-tile stores uncoalesced and bandwidth-limiting
-// (Sec. 5.2.1); here every row segment leaves the SM as contiguous 16-byte
-// chunks.
+// columns from lanes l+1..l+3 with shuffles.  Each output row segment is
+// staged in shared memory and leaves the SM as one bulk copy (TMA) of its
+// 16-byte-aligned body plus a few plain stores for the unaligned ends; a ring
+// of kStoreStages buffers per warp keeps copies in flight while the next rows
+// are computed.  The paper found its one-thread-per-tile stores uncoalesced
+// and bandwidth-limiting (Sec. 5.2.1); here every row leaves as contiguous
+// 16-byte-aligned bulk transfers.
 //
 // Adjoint (transpose of Eq. 1): the same strip walked in the opposite
-// direction -- x-transpose per lane, column gather with shuffles, y and z
-// accumulation in registers -- into per-unit partial sums, reduced afterwards
-// in a fixed order (no atomics, bitwise reproducible).
+// direction.  Rows of the voxel gradient arrive by bulk copy into a ring of
+// kLoadStages buffers per warp (mbarrier completion, issued kLoadStages rows
+// ahead); each lane applies the x-transpose to its tile, a column collects
+// the four tiles that touch it with shuffles, and y and z are accumulated in
+// registers into per-unit partial sums that a second kernel reduces in a
+// fixed order (no atomics, bitwise reproducible).
 #pragma once
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bsi_async.cuh"
 #include "bsi_geometry.h"
 #include "bsi_weights.cuh"
 
 namespace bsi {
 
-constexpr int kWarpsPerCta = 8;                  // at most; fewer when staging buffers are large
-constexpr int kThreads = kWarpsPerCta * kLanes;
-constexpr int kSmemBudget = 200 * 1024;          // dynamic shared memory per CTA we allow
-
-// Warps per CTA such that each warp's two staging buffers fit the budget.
-inline int warps_per_cta(int buf_bytes) {
-    int w = kSmemBudget / (2 * buf_bytes);
-    return w < 1 ? 1 : (w > kWarpsPerCta ? kWarpsPerCta : w);
-}
 constexpr unsigned kFull = 0xffffffffu;
 
-// Kernel error bits (checked builds only).
+// Kernel error bits (range bits only in checked builds; kErrTimeout always).
 enum : unsigned {
     kErrPhiRead = 1u,
     kErrFieldWrite = 2u,
@@ -51,6 +48,7 @@ enum : unsigned {
     kErrPartWrite = 16u,
     kErrPartRead = 32u,
     kErrDphiWrite = 64u,
+    kErrTimeout = 128u,
 };
 
 #ifdef BSI_CHECKED
@@ -62,66 +60,69 @@ enum : unsigned {
 #define BSI_GUARD(cond, bit, err)
 #endif
 
-// ------------------------------------------------------------------ copies
-
-// Stores nbytes from shared s to global g; s and g are congruent mod 16.  The
-// 16-byte-aligned body goes out as one coalesced uint4 per lane per step;
-// the unaligned head and tail (< 16 bytes each) as ES-byte elements.
-template <int ES>
-__device__ __forceinline__ void copy_out(const unsigned char* s, unsigned char* g, int nbytes,
-                                         int lane) {
-    const int mis = (int)((uintptr_t)g & 15);
-    int head = mis ? 16 - mis : 0;
-    if (head > nbytes) head = nbytes;
-    const int nbody = (nbytes - head) >> 4;
-    const int tail = nbytes - head - (nbody << 4);
-    const uint4* sb = reinterpret_cast<const uint4*>(s + head);
-    uint4* gb = reinterpret_cast<uint4*>(g + head);
-    for (int i = lane; i < nbody; i += kLanes) __stcs(gb + i, sb[i]);
-    const int nh = head / ES, nt = tail / ES;
-    int off = -1;
-    if (lane < nh) off = lane * ES;
-    else if (lane < nh + nt) off = head + (nbody << 4) + (lane - nh) * ES;
-    if (off >= 0) {
-        if (ES == 4) *reinterpret_cast<uint32_t*>(g + off) = *reinterpret_cast<const uint32_t*>(s + off);
-        else *reinterpret_cast<uint16_t*>(g + off) = *reinterpret_cast<const uint16_t*>(s + off);
-    }
-}
-
-// Loads nbytes (multiple of 4) from global g into shared s; congruent mod 16.
-__device__ __forceinline__ void copy_in(unsigned char* s, const unsigned char* g, int nbytes,
-                                        int lane) {
-    const int mis = (int)((uintptr_t)g & 15);
-    int head = mis ? 16 - mis : 0;
-    if (head > nbytes) head = nbytes;
-    const int nbody = (nbytes - head) >> 4;
-    const int tail = nbytes - head - (nbody << 4);
-    const uint4* gb = reinterpret_cast<const uint4*>(g + head);
-    uint4* sb = reinterpret_cast<uint4*>(s + head);
-    for (int i = lane; i < nbody; i += kLanes) sb[i] = gb[i];
-    const int nh = head >> 2, nt = tail >> 2;
-    int off = -1;
-    if (lane < nh) off = lane * 4;
-    else if (lane < nh + nt) off = head + (nbody << 4) + (lane - nh) * 4;
-    if (off >= 0)
-        *reinterpret_cast<uint32_t*>(s + off) = *reinterpret_cast<const uint32_t*>(g + off);
-}
+__device__ __forceinline__ uintptr_t floor16(uintptr_t a) { return a & ~(uintptr_t)15; }
+__device__ __forceinline__ uintptr_t ceil16(uintptr_t a) { return (a + 15) & ~(uintptr_t)15; }
 
 template <bool BF16>
-__device__ __forceinline__ void put_elem(unsigned char* s, int e, float v) {
-    if (BF16) reinterpret_cast<__nv_bfloat16*>(s)[e] = __float2bfloat16_rn(v);
-    else reinterpret_cast<float*>(s)[e] = v;
+__device__ __forceinline__ void put3(unsigned char* s, int e, float a, float b, float c) {
+    if (BF16) {
+        __nv_bfloat16* p = reinterpret_cast<__nv_bfloat16*>(s) + e;
+        p[0] = __float2bfloat16_rn(a);
+        p[1] = __float2bfloat16_rn(b);
+        p[2] = __float2bfloat16_rn(c);
+    } else {
+        float* p = reinterpret_cast<float*>(s) + e;
+        p[0] = a;
+        p[1] = b;
+        p[2] = c;
+    }
 }
 
 // ------------------------------------------------------------------ forward
 
+// Writes one staged row segment [g, g + nbytes) (staged at sb, congruent to g
+// mod 16): lane 0 hands the 16-byte-aligned body to the bulk-copy engine and
+// commits one bulk group; lanes store the < 16-byte head and tail themselves.
+template <int ES>
+__device__ __forceinline__ void store_row(const unsigned char* sb, unsigned char* g, int nbytes, int lane) {
+    const uintptr_t ga = reinterpret_cast<uintptr_t>(g);
+    const uintptr_t a = ceil16(ga), e = ga + (uintptr_t)nbytes;
+    const uintptr_t b = floor16(e) > a ? floor16(e) : a;
+    int head = (int)(a - ga);
+    if (head > nbytes) head = nbytes;
+    const int body = (int)(b - a);
+    if (lane == 0) {
+        if (body > 0) bulk_store(g + head, sb + head, (uint32_t)body);
+        bulk_commit();
+    }
+    const int tail = nbytes - head - body;
+    const int nh = head / ES, nt = tail / ES;
+    int off = -1;
+    if (lane < nh) off = lane * ES;
+    else if (lane < nh + nt) off = head + body + (lane - nh) * ES;
+    if (off >= 0) {
+        if (ES == 4) *reinterpret_cast<uint32_t*>(g + off) = *reinterpret_cast<const uint32_t*>(sb + off);
+        else *reinterpret_cast<uint16_t*>(g + off) = *reinterpret_cast<const uint16_t*>(sb + off);
+    }
+}
+
+// x-stage of one voxel of a tile: out = sum_l B_l(r/dx) p_l, per channel.
+template <bool BF16>
+__device__ __forceinline__ void emit_voxel(unsigned char* sb, int e, int wo, const float (&p0)[3],
+                                           const float (&p1)[3], const float (&p2)[3], const float (&p3)[3]) {
+    const float w0 = c_lut.w[wo], w1 = c_lut.w[wo + 1], w2 = c_lut.w[wo + 2], w3 = c_lut.w[wo + 3];
+    put3<BF16>(sb, e, fmaf(w3, p3[0], fmaf(w2, p2[0], fmaf(w1, p1[0], w0 * p0[0]))),
+               fmaf(w3, p3[1], fmaf(w2, p2[1], fmaf(w1, p1[1], w0 * p0[1]))),
+               fmaf(w3, p3[2], fmaf(w2, p2[2], fmaf(w1, p1[2], w0 * p0[2]))));
+}
+
 // One forward unit: tile-plane kz, tile-row jy, x-group xg.  DX > 0 is a
-// compile-time x-spacing (fully unrolled inner loop, weights as constant
-// operands); DX == 0 reads the spacing at run time.
+// compile-time x-spacing (unrolled inner loop, weights as constant operands);
+// DX == 0 reads the spacing at run time.  rowc counts the rows this warp has
+// staged so far (it selects the ring buffer).
 template <int DX, bool BF16>
-__device__ __forceinline__ void forward_unit(const WeightTable& lut, const InstDesc& d,
-                                             long long ul, unsigned char* stage, int buf_bytes,
-                                             int lane, int& par, unsigned* err) {
+__device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, unsigned char* stage,
+                                             int buf_bytes, int lane, unsigned& rowc, unsigned* err) {
     constexpr int ES = BF16 ? 2 : 4;
     const int dx = DX > 0 ? DX : d.dx;
     const FwdUnit u = fwd_unit(d, ul);
@@ -150,15 +151,15 @@ __device__ __forceinline__ void forward_unit(const WeightTable& lut, const InstD
 
     const int z0 = u.kz * d.dz, zn = imin(d.dz, d.Z - z0);
     const int y0 = u.jy * d.dy, yn = imin(d.dy, d.Y - y0);
-    const float* wz = lut.w + weight_base(d.dz);
-    const float* wy = lut.w + weight_base(d.dy);
-    const float* wx = lut.w + weight_base(dx);
-    const int xl = lane * dx;             // first strip voxel of this lane's tile
+    const int wzb = weight_base(d.dz), wyb = weight_base(d.dy), wxb = weight_base(dx);
+    const int xl = lane * dx;                 // first strip voxel of this lane's tile
     const bool emits = lane < u.ncell;
+    const bool full = emits && xl + dx <= u.nvox;
     const int nbytes = u.nvox * 3 * ES;
 
     for (int rz = 0; rz < zn; ++rz) {
-        const float a0 = wz[4 * rz], a1 = wz[4 * rz + 1], a2 = wz[4 * rz + 2], a3 = wz[4 * rz + 3];
+        const float a0 = c_lut.w[wzb + 4 * rz], a1 = c_lut.w[wzb + 4 * rz + 1];
+        const float a2 = c_lut.w[wzb + 4 * rz + 2], a3 = c_lut.w[wzb + 4 * rz + 3];
         float pz[4][3];
 #pragma unroll
         for (int m = 0; m < 4; ++m)
@@ -167,7 +168,8 @@ __device__ __forceinline__ void forward_unit(const WeightTable& lut, const InstD
                 pz[m][c] = fmaf(a3, ph[3][m][c], fmaf(a2, ph[2][m][c], fmaf(a1, ph[1][m][c], a0 * ph[0][m][c])));
 
         for (int ry = 0; ry < yn; ++ry) {
-            const float b0 = wy[4 * ry], b1 = wy[4 * ry + 1], b2 = wy[4 * ry + 2], b3 = wy[4 * ry + 3];
+            const float b0 = c_lut.w[wyb + 4 * ry], b1 = c_lut.w[wyb + 4 * ry + 1];
+            const float b2 = c_lut.w[wyb + 4 * ry + 2], b3 = c_lut.w[wyb + 4 * ry + 3];
             float p0[3], p1[3], p2[3], p3[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -179,38 +181,27 @@ __device__ __forceinline__ void forward_unit(const WeightTable& lut, const InstD
 
             const long long e0 = field_elem(d, z0 + rz, y0 + ry, u.x0);
             unsigned char* g = static_cast<unsigned char*>(d.field) + e0 * ES;
-            const int shift = (int)((uintptr_t)g & 15);
-            unsigned char* sbuf = stage + par * buf_bytes + shift;
-            par ^= 1;
+            const int shift = (int)(reinterpret_cast<uintptr_t>(g) & 15);
+            unsigned char* sb = stage + (rowc % kStoreStages) * buf_bytes + shift;
+            ++rowc;
+            // the bulk copy that last read this ring buffer must be done with it
+            if (lane == 0) bulk_wait_read<kStoreStages - 1>();
+            __syncwarp();
             BSI_GUARD(shift + nbytes <= buf_bytes, kErrStage, err) {
-                if (emits) {
-                    if (DX > 0) {
+                if (DX > 0 && full) {
 #pragma unroll
-                        for (int r = 0; r < (DX > 0 ? DX : 1); ++r) {
-                            if (xl + r < u.nvox) {
-                                const float w0 = wx[4 * r], w1 = wx[4 * r + 1], w2 = wx[4 * r + 2], w3 = wx[4 * r + 3];
-#pragma unroll
-                                for (int c = 0; c < 3; ++c)
-                                    put_elem<BF16>(sbuf, (xl + r) * 3 + c,
-                                                   fmaf(w3, p3[c], fmaf(w2, p2[c], fmaf(w1, p1[c], w0 * p0[c]))));
-                            }
-                        }
-                    } else {
-                        const int rn = imin(dx, u.nvox - xl);
-                        for (int r = 0; r < rn; ++r) {
-                            const float w0 = wx[4 * r], w1 = wx[4 * r + 1], w2 = wx[4 * r + 2], w3 = wx[4 * r + 3];
-#pragma unroll
-                            for (int c = 0; c < 3; ++c)
-                                put_elem<BF16>(sbuf, (xl + r) * 3 + c,
-                                               fmaf(w3, p3[c], fmaf(w2, p2[c], fmaf(w1, p1[c], w0 * p0[c]))));
-                        }
-                    }
+                    for (int r = 0; r < (DX > 0 ? DX : 1); ++r)
+                        emit_voxel<BF16>(sb, (xl + r) * 3, weight_base(DX > 0 ? DX : 1) + 4 * r, p0, p1, p2, p3);
+                } else if (emits) {  // run-time spacing, or the tile cut by the volume's x-end
+                    const int rn = imin(dx, u.nvox - xl);
+                    for (int r = 0; r < rn; ++r) emit_voxel<BF16>(sb, (xl + r) * 3, wxb + 4 * r, p0, p1, p2, p3);
                 }
             }
+            fence_proxy_async_smem();  // this lane's staging writes before the bulk copy reads them
             __syncwarp();
             BSI_GUARD(e0 >= 0 && e0 + 3LL * u.nvox <= 3LL * d.X * d.Y * d.Z && shift + nbytes <= buf_bytes,
                       kErrFieldWrite, err) {
-                copy_out<ES>(sbuf, g, nbytes, lane);
+                store_row<ES>(sb, g, nbytes, lane);
             }
         }
     }
@@ -237,9 +228,41 @@ __device__ __forceinline__ void flush_plane(const InstDesc& d, long long ul, int
     }
 }
 
+// Bulk-load plan of one gradient row segment [g, g + nbytes): the copy covers
+// [s0, s1), the 16-byte-aligned superset of the segment clipped to the
+// 16-byte-aligned interior [A0, A1) of the gradient array, and lands in the
+// ring buffer at offset s0 - floor16(g); element e of the row then sits at
+// offset (g - floor16(g)) + 4e.  Bytes of the segment outside [s0, s1) exist
+// only at the two ends of the array and are loaded by lanes.
+struct RowLoad {
+    uintptr_t g, lo, s0, s1;
+};
+
+__device__ __forceinline__ RowLoad row_load(const unsigned char* g, int nbytes, uintptr_t A0, uintptr_t A1) {
+    RowLoad r;
+    r.g = reinterpret_cast<uintptr_t>(g);
+    r.lo = floor16(r.g);
+    r.s0 = r.lo > A0 ? r.lo : A0;
+    const uintptr_t hi = ceil16(r.g + (uintptr_t)nbytes);
+    r.s1 = hi < A1 ? hi : A1;
+    return r;
+}
+
+// x-transpose of one voxel: q_l += B_l(r/dx) g, per channel.
+__device__ __forceinline__ void gather_voxel(float (&q4)[4][3], const float* sv, int wo) {
+    const float g0 = sv[0], g1 = sv[1], g2 = sv[2];
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        const float w = c_lut.w[wo + l];
+        q4[l][0] = fmaf(w, g0, q4[l][0]);
+        q4[l][1] = fmaf(w, g1, q4[l][1]);
+        q4[l][2] = fmaf(w, g2, q4[l][2]);
+    }
+}
+
 template <int DX>
-__device__ __forceinline__ void adjoint_unit(const WeightTable& lut, const InstDesc& d, long long ul,
-                                             unsigned char* stage, int buf_bytes, int lane, int& par,
+__device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, uint64_t* bars,
+                                             unsigned char* bufs, int buf_bytes, int lane, unsigned& q,
                                              float* part, long long ws_floats, unsigned* err) {
     const int dx = DX > 0 ? DX : d.dx;
     const AdjUnit u = adj_unit(d, ul);
@@ -247,10 +270,30 @@ __device__ __forceinline__ void adjoint_unit(const WeightTable& lut, const InstD
     const int nv = (cell >= 0 && cell < d.ncx) ? imin(dx, d.X - cell * dx) : 0;
     const int xl = cell * dx - u.xs;      // strip-local first voxel of this lane's tile
     const int y0 = u.jy * d.dy, yn = imin(d.dy, d.Y - y0);
-    const float* wz = lut.w + weight_base(d.dz);
-    const float* wy = lut.w + weight_base(d.dy);
-    const float* wx = lut.w + weight_base(dx);
+    const int zb = u.kz0 * d.dz;
+    const int rows = (imin(u.kz1 * d.dz, d.Z) - zb) * yn;
+    const int wxb = weight_base(dx), wyb = weight_base(d.dy), wzb = weight_base(d.dz);
     const int nbytes = u.nvox * 12;
+    const unsigned char* gbase = reinterpret_cast<const unsigned char*>(d.grad);
+    const uintptr_t A0 = ceil16(reinterpret_cast<uintptr_t>(gbase));
+    const uintptr_t A1 = floor16(reinterpret_cast<uintptr_t>(gbase) + (uintptr_t)(12LL * d.X * d.Y * d.Z));
+    const unsigned q0 = q;
+
+    // lane 0 puts row k of this unit in flight into ring buffer (q0 + k) % kLoadStages
+    auto issue = [&](int k) {
+        const unsigned st = (q0 + (unsigned)k) % kLoadStages;
+        const unsigned char* g = gbase + 4 * field_elem(d, zb + k / yn, y0 + k % yn, u.xs);
+        const RowLoad L = row_load(g, nbytes, A0, A1);
+        if (L.s1 > L.s0) {
+            mbar_arrive_expect_tx(&bars[st], (uint32_t)(L.s1 - L.s0));
+            bulk_load(bufs + st * buf_bytes + (L.s0 - L.lo), reinterpret_cast<const void*>(L.s0),
+                      (uint32_t)(L.s1 - L.s0), &bars[st]);
+        } else {
+            mbar_arrive(&bars[st]);
+        }
+    };
+    if (lane == 0)
+        for (int k = 0; k < rows && k < kLoadStages; ++k) issue(k);
 
     float hz[4][4][3];
 #pragma unroll
@@ -260,6 +303,7 @@ __device__ __forceinline__ void adjoint_unit(const WeightTable& lut, const InstD
 #pragma unroll
             for (int c = 0; c < 3; ++c) hz[n][m][c] = 0.f;
 
+    int k = 0;
     for (int kz = u.kz0; kz < u.kz1; ++kz) {
         const int z0 = kz * d.dz, zn = imin(d.dz, d.Z - z0);
         for (int rz = 0; rz < zn; ++rz) {
@@ -269,62 +313,68 @@ __device__ __forceinline__ void adjoint_unit(const WeightTable& lut, const InstD
 #pragma unroll
                 for (int c = 0; c < 3; ++c) hy[m][c] = 0.f;
 
-            for (int ry = 0; ry < yn; ++ry) {
+            for (int ry = 0; ry < yn; ++ry, ++k) {
+                const unsigned qq = q0 + (unsigned)k;
+                const unsigned st = qq % kLoadStages;
+                if (!mbar_wait_bounded(&bars[st], (qq / kLoadStages) & 1u)) {
+                    // a bulk copy never completed: record it, give the copies still
+                    // in flight a bounded chance to land, and stop this warp
+                    if (lane == 0) atomicOr(err, kErrTimeout);
+                    for (int p = k + 1; p < rows && p < k + kLoadStages; ++p) {
+                        const unsigned qp = q0 + (unsigned)p;
+                        (void)mbar_wait_bounded(&bars[qp % kLoadStages], (qp / kLoadStages) & 1u);
+                    }
+                    q = q0 + (unsigned)rows;
+                    return false;
+                }
                 const long long e0 = field_elem(d, z0 + rz, y0 + ry, u.xs);
-                const unsigned char* g = reinterpret_cast<const unsigned char*>(d.grad + e0);
-                const int shift = (int)((uintptr_t)g & 15);
-                unsigned char* sbuf = stage + par * buf_bytes + shift;
-                par ^= 1;
-                BSI_GUARD(e0 >= 0 && e0 + 3LL * u.nvox <= 3LL * d.X * d.Y * d.Z && shift + nbytes <= buf_bytes,
+                const RowLoad L = row_load(gbase + 4 * e0, nbytes, A0, A1);
+                unsigned char* sb = bufs + st * buf_bytes + (L.g - L.lo);
+                BSI_GUARD((int)(L.g - L.lo) + nbytes <= buf_bytes && e0 + 3LL * u.nvox <= 3LL * d.X * d.Y * d.Z,
                           kErrGradRead, err) {
-                    copy_in(sbuf, g, nbytes, lane);
+                    if (L.g < L.s0 || L.g + (uintptr_t)nbytes > L.s1) {
+                        // first or last row of the array: elements outside the bulk copy
+                        for (int i = lane; i < u.nvox * 3; i += kLanes) {
+                            const uintptr_t a = L.g + 4u * (uintptr_t)i;
+                            if (a < L.s0 || a >= L.s1)
+                                reinterpret_cast<float*>(sb)[i] = *reinterpret_cast<const float*>(a);
+                        }
+                    }
                 }
                 __syncwarp();
-                const float* sv = reinterpret_cast<const float*>(sbuf);
-                float q[4][3];
+                const float* sv = reinterpret_cast<const float*>(sb) + xl * 3;
+                float q4[4][3];
 #pragma unroll
                 for (int l = 0; l < 4; ++l)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) q[l][c] = 0.f;
-                if (DX > 0) {
+                    for (int c = 0; c < 3; ++c) q4[l][c] = 0.f;
+                if (DX > 0 && nv == DX) {
 #pragma unroll
-                    for (int r = 0; r < (DX > 0 ? DX : 1); ++r) {
-                        if (r < nv) {
-                            const float g0 = sv[(xl + r) * 3], g1 = sv[(xl + r) * 3 + 1], g2 = sv[(xl + r) * 3 + 2];
-#pragma unroll
-                            for (int l = 0; l < 4; ++l) {
-                                const float w = wx[4 * r + l];
-                                q[l][0] = fmaf(w, g0, q[l][0]);
-                                q[l][1] = fmaf(w, g1, q[l][1]);
-                                q[l][2] = fmaf(w, g2, q[l][2]);
-                            }
-                        }
-                    }
+                    for (int r = 0; r < (DX > 0 ? DX : 1); ++r)
+                        gather_voxel(q4, sv + 3 * r, weight_base(DX > 0 ? DX : 1) + 4 * r);
                 } else {
-                    for (int r = 0; r < nv; ++r) {
-                        const float g0 = sv[(xl + r) * 3], g1 = sv[(xl + r) * 3 + 1], g2 = sv[(xl + r) * 3 + 2];
-#pragma unroll
-                        for (int l = 0; l < 4; ++l) {
-                            const float w = wx[4 * r + l];
-                            q[l][0] = fmaf(w, g0, q[l][0]);
-                            q[l][1] = fmaf(w, g1, q[l][1]);
-                            q[l][2] = fmaf(w, g2, q[l][2]);
-                        }
-                    }
+                    for (int r = 0; r < nv; ++r) gather_voxel(q4, sv + 3 * r, wxb + 4 * r);
                 }
-                // column sum: column of lane l collects q[k] of the tile k lanes below
-                const float b0 = wy[4 * ry], b1 = wy[4 * ry + 1], b2 = wy[4 * ry + 2], b3 = wy[4 * ry + 3];
+                // this ring buffer may be refilled once every lane has read it
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0 && k + kLoadStages < rows) issue(k + kLoadStages);
+
+                // column sum: the column of lane l collects q4[k] of the tile k lanes below
+                const float b0 = c_lut.w[wyb + 4 * ry], b1 = c_lut.w[wyb + 4 * ry + 1];
+                const float b2 = c_lut.w[wyb + 4 * ry + 2], b3 = c_lut.w[wyb + 4 * ry + 3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float h = q[0][c] + __shfl_up_sync(kFull, q[1][c], 1) +
-                                    __shfl_up_sync(kFull, q[2][c], 2) + __shfl_up_sync(kFull, q[3][c], 3);
+                    const float h = q4[0][c] + __shfl_up_sync(kFull, q4[1][c], 1) +
+                                    __shfl_up_sync(kFull, q4[2][c], 2) + __shfl_up_sync(kFull, q4[3][c], 3);
                     hy[0][c] = fmaf(b0, h, hy[0][c]);
                     hy[1][c] = fmaf(b1, h, hy[1][c]);
                     hy[2][c] = fmaf(b2, h, hy[2][c]);
                     hy[3][c] = fmaf(b3, h, hy[3][c]);
                 }
             }
-            const float a0 = wz[4 * rz], a1 = wz[4 * rz + 1], a2 = wz[4 * rz + 2], a3 = wz[4 * rz + 3];
+            const float a0 = c_lut.w[wzb + 4 * rz], a1 = c_lut.w[wzb + 4 * rz + 1];
+            const float a2 = c_lut.w[wzb + 4 * rz + 2], a3 = c_lut.w[wzb + 4 * rz + 3];
 #pragma unroll
             for (int m = 0; m < 4; ++m)
 #pragma unroll
@@ -335,7 +385,7 @@ __device__ __forceinline__ void adjoint_unit(const WeightTable& lut, const InstD
                     hz[3][m][c] = fmaf(a3, hy[m][c], hz[3][m][c]);
                 }
         }
-        // grid plane kz + 0 is complete for this unit; roll the window by one plane
+        // grid plane kz is complete for this unit; roll the window by one plane
         flush_plane(d, ul, kz - u.kz0, u, lane, hz[0], part, ws_floats, err);
 #pragma unroll
         for (int n = 0; n < 3; ++n)
@@ -351,6 +401,8 @@ __device__ __forceinline__ void adjoint_unit(const WeightTable& lut, const InstD
     const int nk = u.kz1 - u.kz0;
 #pragma unroll
     for (int n = 0; n < 3; ++n) flush_plane(d, ul, nk + n, u, lane, hz[n], part, ws_floats, err);
+    q = q0 + (unsigned)rows;
+    return true;
 }
 
 }  // namespace bsi

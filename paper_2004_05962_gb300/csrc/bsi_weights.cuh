@@ -41,4 +41,7 @@ constexpr WeightTable make_weight_table() {
     return t;
 }
 
+// One copy in the constant bank of every translation unit that includes this header.
+static __constant__ WeightTable c_lut = make_weight_table();
+
 }  // namespace bsi
