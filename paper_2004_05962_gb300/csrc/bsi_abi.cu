@@ -67,7 +67,10 @@ cudaError_t kernel_facts(const void* kernel, int threads, int smem, KernelFacts*
 
 // ----------------------------------------------------------- planning
 
+// Tile-planes per adjoint unit.  Must be >= 3: the reduce kernel then finds
+// every grid plane in at most two consecutive chunks.
 constexpr int kDefaultZChunk = 4;
+static_assert(kDefaultZChunk >= 3, "adjoint reduce assumes chunks of at least 3 tile-planes");
 
 static thread_local char t_cuda_msg[256] = "";
 

@@ -31,6 +31,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
     const long long nwarps = (long long)gridDim.x * wpc;
     int ii = 0;
     unsigned q = 0;
+    // CTA-major slots: the warps of a CTA take neighbouring units (in a batch,
+    // the same kernel specialisation)
     for (long long uu = (long long)blockIdx.x * wpc + warp; uu < b.total_units; uu += nwarps) {
         while (ii + 1 < b.n && uu >= b.inst[ii + 1].unit_begin) ++ii;
         const InstDesc& d = b.inst[ii];
@@ -82,25 +84,39 @@ __global__ void __launch_bounds__(256)
         const int xg = gx / kGroupCells, j = gx - xg * kGroupCells;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
         if (d.nzc > 0) {
+            // The covering partials: at most two tile-plane chunks (zc_hi - 1, zc_hi)
+            // times four tile-rows.  All 8 x 3 loads are issued before any sum, and
+            // the sum runs in the fixed order (chunk, row).
             const int zc_hi = imin(d.nzc - 1, gz / d.zchunk);
-            const int zc_lo = gz - d.zchunk - kHalo + 1 > 0 ? (int)cdiv(gz - d.zchunk - kHalo + 1, d.zchunk) : 0;
-            for (int zc = zc_lo; zc <= zc_hi; ++zc) {
+            float v[2][4][3];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int zc = zc_hi - 1 + t;
                 const int pz = gz - zc * d.zchunk;
-                const int planes = imin(d.zchunk, d.ncz - zc * d.zchunk) + kHalo;
-                if (pz >= planes) continue;
+                const bool zok = zc >= 0 && pz < imin(d.zchunk, d.ncz - zc * d.zchunk) + kHalo;
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     const int jy = gy - m;
-                    if (jy < 0 || jy >= d.ncy) continue;
-                    const long long ul = ((long long)zc * d.ncy + jy) * d.nxg + xg;
-                    const long long e = part_elem(d, ul, pz, m, j);
-                    BSI_GUARD(e >= 0 && e + 3 <= ws_floats, kErrPartRead, &g_err) {
-                        s0 += part[e];
-                        s1 += part[e + 1];
-                        s2 += part[e + 2];
+                    v[t][m][0] = v[t][m][1] = v[t][m][2] = 0.f;
+                    if (zok && jy >= 0 && jy < d.ncy) {
+                        const long long ul = ((long long)zc * d.ncy + jy) * d.nxg + xg;
+                        const long long e = part_elem(d, ul, pz, m, j);
+                        BSI_GUARD(e >= 0 && e + 3 <= ws_floats, kErrPartRead, &g_err) {
+                            v[t][m][0] = __ldcs(part + e);
+                            v[t][m][1] = __ldcs(part + e + 1);
+                            v[t][m][2] = __ldcs(part + e + 2);
+                        }
                     }
                 }
             }
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    s0 += v[t][m][0];
+                    s1 += v[t][m][1];
+                    s2 += v[t][m][2];
+                }
         }
         float* o = d.dphi + pl * 3;
         BSI_GUARD(pl >= 0 && pl < (long long)d.nx * d.ny * d.nz, kErrDphiWrite, &g_err) {

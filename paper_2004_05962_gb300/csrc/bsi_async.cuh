@@ -16,7 +16,8 @@
 
 namespace bsi {
 
-constexpr int kSpinLimit = 1 << 22;   // try_wait rounds before a wait is declared lost
+constexpr uint32_t kSuspendHintNs = 100000;   // longest sleep of one try_wait round
+constexpr int kSpinLimit = 20000;              // try_wait rounds before a wait is declared lost
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -74,18 +75,21 @@ __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t
                  :: "r"(smem_u32(sdst)), "l"(gsrc), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
+// One bounded wait round: the thread may sleep up to kSuspendHintNs for the
+// phase of `parity` to complete (it wakes when it does); true if it completed.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendHintNs) : "memory");
     return ok != 0;
 }
 
-// Waits for the phase of `parity` to complete, at most kSpinLimit rounds.
-// Returns false (warp-uniformly) if any lane gave up.
+// Waits for the phase of `parity` to complete, at most kSpinLimit rounds of
+// at most kSuspendHintNs each (about 2 s in all).  Returns false
+// (warp-uniformly) if any lane gave up.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
     bool ok = false;
     for (int i = 0; i < kSpinLimit && !ok; ++i) ok = mbar_try_wait(bar, parity);

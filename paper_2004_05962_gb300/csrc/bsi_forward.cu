@@ -6,8 +6,9 @@ namespace bsi {
 
 static __device__ unsigned g_err;
 
-// Persistent grid: warp w of the launch takes units w, w + W, w + 2W, ... of
-// the concatenated unit lists of all instances (W = warps in the grid).  The
+// Persistent grid: the warp in slot w = blockIdx.x * warps_per_cta + warp takes
+// units w, w + W, w + 2W, ... of the concatenated unit lists of all instances
+// (W = warps in the grid).  The
 // per-unit work is near-uniform, so the static stride balances without an
 // atomic ticket and is deterministic.
 template <int MAXB, bool BF16, bool GENERIC>
@@ -20,23 +21,25 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
     const int wpc = blockDim.x >> 5;
     const long long nwarps = (long long)gridDim.x * wpc;
     int ii = 0;
-    unsigned rowc = 0;
+    int ring = 0;  // next staging buffer of the warp's store ring
+    // CTA-major slots: the warps of a CTA take neighbouring units, which share
+    // control-point columns in L1 and, in a batch, the same kernel specialisation
     for (long long uu = (long long)blockIdx.x * wpc + warp; uu < b.total_units; uu += nwarps) {
         while (ii + 1 < b.n && uu >= b.inst[ii + 1].unit_begin) ++ii;
         const InstDesc& d = b.inst[ii];
         const long long ul = uu - d.unit_begin;
         if (GENERIC) {
-            forward_unit<0, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err);
+            forward_unit<0, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err);
         } else {
             switch (d.dx) {
-                case 1: forward_unit<1, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
-                case 2: forward_unit<2, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
-                case 3: forward_unit<3, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
-                case 4: forward_unit<4, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
-                case 5: forward_unit<5, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
-                case 6: forward_unit<6, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
-                case 7: forward_unit<7, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
-                default: forward_unit<8, BF16>(d, ul, stage, b.buf_bytes, lane, rowc, &g_err); break;
+                case 1: forward_unit<1, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 2: forward_unit<2, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 3: forward_unit<3, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 4: forward_unit<4, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 5: forward_unit<5, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 6: forward_unit<6, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 7: forward_unit<7, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                default: forward_unit<8, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
             }
         }
     }

@@ -81,26 +81,24 @@ __device__ __forceinline__ void put3(unsigned char* s, int e, float a, float b, 
 // ------------------------------------------------------------------ forward
 
 // Writes one staged row segment [g, g + nbytes) (staged at sb, congruent to g
-// mod 16): lane 0 hands the 16-byte-aligned body to the bulk-copy engine and
-// commits one bulk group; lanes store the < 16-byte head and tail themselves.
+// mod 16; shift = g mod 16): lane 0 hands the 16-byte-aligned body to the
+// bulk-copy engine, commits one bulk group and then waits until at most
+// kStoreStages - 1 groups still read shared memory, which frees the ring
+// buffer the warp writes next; lanes store the < 16-byte head and tail.
 template <int ES>
-__device__ __forceinline__ void store_row(const unsigned char* sb, unsigned char* g, int nbytes, int lane) {
-    const uintptr_t ga = reinterpret_cast<uintptr_t>(g);
-    const uintptr_t a = ceil16(ga), e = ga + (uintptr_t)nbytes;
-    const uintptr_t b = floor16(e) > a ? floor16(e) : a;
-    int head = (int)(a - ga);
-    if (head > nbytes) head = nbytes;
-    const int body = (int)(b - a);
+__device__ __forceinline__ void store_row(const unsigned char* sb, unsigned char* g, int shift, int nbytes,
+                                          int lane) {
+    int head = (16 - shift) & 15;
+    head = head < nbytes ? head : nbytes;
+    const int body = (nbytes - head) & ~15;
     if (lane == 0) {
         if (body > 0) bulk_store(g + head, sb + head, (uint32_t)body);
         bulk_commit();
+        bulk_wait_read<kStoreStages - 1>();
     }
-    const int tail = nbytes - head - body;
-    const int nh = head / ES, nt = tail / ES;
-    int off = -1;
-    if (lane < nh) off = lane * ES;
-    else if (lane < nh + nt) off = head + body + (lane - nh) * ES;
-    if (off >= 0) {
+    const int nh = head / ES, nt = (nbytes - head - body) / ES;
+    const int off = lane < nh ? lane * ES : head + body + (lane - nh) * ES;
+    if (lane < nh + nt) {
         if (ES == 4) *reinterpret_cast<uint32_t*>(g + off) = *reinterpret_cast<const uint32_t*>(sb + off);
         else *reinterpret_cast<uint16_t*>(g + off) = *reinterpret_cast<const uint16_t*>(sb + off);
     }
@@ -118,11 +116,11 @@ __device__ __forceinline__ void emit_voxel(unsigned char* sb, int e, int wo, con
 
 // One forward unit: tile-plane kz, tile-row jy, x-group xg.  DX > 0 is a
 // compile-time x-spacing (unrolled inner loop, weights as constant operands);
-// DX == 0 reads the spacing at run time.  rowc counts the rows this warp has
-// staged so far (it selects the ring buffer).
+// DX == 0 reads the spacing at run time.  ring is the warp's next staging
+// buffer in its store ring (0 .. kStoreStages - 1).
 template <int DX, bool BF16>
 __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, unsigned char* stage,
-                                             int buf_bytes, int lane, unsigned& rowc, unsigned* err) {
+                                             int buf_bytes, int lane, int& ring, unsigned* err) {
     constexpr int ES = BF16 ? 2 : 4;
     const int dx = DX > 0 ? DX : d.dx;
     const FwdUnit u = fwd_unit(d, ul);
@@ -156,8 +154,11 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
     const bool emits = lane < u.ncell;
     const bool full = emits && xl + dx <= u.nvox;
     const int nbytes = u.nvox * 3 * ES;
+    const long long row_pitch = 3LL * d.X * ES;          // bytes from row y to row y + 1
+    const long long plane_pitch = row_pitch * d.Y;       // bytes from plane z to plane z + 1
+    unsigned char* gplane = static_cast<unsigned char*>(d.field) + field_elem(d, z0, y0, u.x0) * ES;
 
-    for (int rz = 0; rz < zn; ++rz) {
+    for (int rz = 0; rz < zn; ++rz, gplane += plane_pitch) {
         const float a0 = c_lut.w[wzb + 4 * rz], a1 = c_lut.w[wzb + 4 * rz + 1];
         const float a2 = c_lut.w[wzb + 4 * rz + 2], a3 = c_lut.w[wzb + 4 * rz + 3];
         float pz[4][3];
@@ -167,7 +168,8 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
             for (int c = 0; c < 3; ++c)
                 pz[m][c] = fmaf(a3, ph[3][m][c], fmaf(a2, ph[2][m][c], fmaf(a1, ph[1][m][c], a0 * ph[0][m][c])));
 
-        for (int ry = 0; ry < yn; ++ry) {
+        unsigned char* g = gplane;
+        for (int ry = 0; ry < yn; ++ry, g += row_pitch) {
             const float b0 = c_lut.w[wyb + 4 * ry], b1 = c_lut.w[wyb + 4 * ry + 1];
             const float b2 = c_lut.w[wyb + 4 * ry + 2], b3 = c_lut.w[wyb + 4 * ry + 3];
             float p0[3], p1[3], p2[3], p3[3];
@@ -179,14 +181,10 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
                 p3[c] = __shfl_down_sync(kFull, p0[c], 3);
             }
 
-            const long long e0 = field_elem(d, z0 + rz, y0 + ry, u.x0);
-            unsigned char* g = static_cast<unsigned char*>(d.field) + e0 * ES;
             const int shift = (int)(reinterpret_cast<uintptr_t>(g) & 15);
-            unsigned char* sb = stage + (rowc % kStoreStages) * buf_bytes + shift;
-            ++rowc;
-            // the bulk copy that last read this ring buffer must be done with it
-            if (lane == 0) bulk_wait_read<kStoreStages - 1>();
-            __syncwarp();
+            unsigned char* sb = stage + ring * buf_bytes + shift;
+            ring = ring == kStoreStages - 1 ? 0 : ring + 1;
+            // (the ring buffer is free: store_row of the previous row waited for it)
             BSI_GUARD(shift + nbytes <= buf_bytes, kErrStage, err) {
                 if (DX > 0 && full) {
 #pragma unroll
@@ -199,10 +197,12 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
             }
             fence_proxy_async_smem();  // this lane's staging writes before the bulk copy reads them
             __syncwarp();
-            BSI_GUARD(e0 >= 0 && e0 + 3LL * u.nvox <= 3LL * d.X * d.Y * d.Z && shift + nbytes <= buf_bytes,
+            BSI_GUARD((g - static_cast<unsigned char*>(d.field)) / ES + 3LL * u.nvox <= 3LL * d.X * d.Y * d.Z &&
+                          g >= static_cast<unsigned char*>(d.field) && shift + nbytes <= buf_bytes,
                       kErrFieldWrite, err) {
-                store_row<ES>(sb, g, nbytes, lane);
+                store_row<ES>(sb, g, shift, nbytes, lane);
             }
+            __syncwarp();  // lane 0's ring wait in store_row precedes every lane's next staging write
         }
     }
 }
@@ -274,16 +274,21 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
     const int rows = (imin(u.kz1 * d.dz, d.Z) - zb) * yn;
     const int wxb = weight_base(dx), wyb = weight_base(d.dy), wzb = weight_base(d.dz);
     const int nbytes = u.nvox * 12;
-    const unsigned char* gbase = reinterpret_cast<const unsigned char*>(d.grad);
-    const uintptr_t A0 = ceil16(reinterpret_cast<uintptr_t>(gbase));
-    const uintptr_t A1 = floor16(reinterpret_cast<uintptr_t>(gbase) + (uintptr_t)(12LL * d.X * d.Y * d.Z));
+    const long long row_pitch = 12LL * d.X;              // bytes from row y to row y + 1
+    const long long plane_pitch = row_pitch * d.Y;       // bytes from plane z to plane z + 1
+    const uintptr_t gbase = reinterpret_cast<uintptr_t>(d.grad);
+    const uintptr_t A0 = ceil16(gbase);
+    const uintptr_t A1 = floor16(gbase + (uintptr_t)(12LL * d.X * d.Y * d.Z));
+    const uintptr_t g_first = gbase + 4 * field_elem(d, zb, y0, u.xs);   // row 0 of the unit
     const unsigned q0 = q;
 
-    // lane 0 puts row k of this unit in flight into ring buffer (q0 + k) % kLoadStages
-    auto issue = [&](int k) {
-        const unsigned st = (q0 + (unsigned)k) % kLoadStages;
-        const unsigned char* g = gbase + 4 * field_elem(d, zb + k / yn, y0 + k % yn, u.xs);
-        const RowLoad L = row_load(g, nbytes, A0, A1);
+    // Producer (lane 0): puts the unit's rows in flight in order, row k into ring
+    // buffer (q0 + k) % kLoadStages; ig / iy / ik track the next row to issue.
+    uintptr_t ig = g_first;
+    int iy = 0, ik = 0;
+    auto issue_next = [&]() {
+        const unsigned st = (q0 + (unsigned)ik) % kLoadStages;
+        const RowLoad L = row_load(reinterpret_cast<const unsigned char*>(ig), nbytes, A0, A1);
         if (L.s1 > L.s0) {
             mbar_arrive_expect_tx(&bars[st], (uint32_t)(L.s1 - L.s0));
             bulk_load(bufs + st * buf_bytes + (L.s0 - L.lo), reinterpret_cast<const void*>(L.s0),
@@ -291,9 +296,16 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
         } else {
             mbar_arrive(&bars[st]);
         }
+        ++ik;
+        ig += row_pitch;
+        if (++iy == yn) {
+            iy = 0;
+            ig += plane_pitch - yn * row_pitch;
+        }
     };
     if (lane == 0)
-        for (int k = 0; k < rows && k < kLoadStages; ++k) issue(k);
+        for (int k = 0; k < rows && k < kLoadStages; ++k) issue_next();
+    uintptr_t gz = g_first;   // consumer: first row of the current voxel plane
 
     float hz[4][4][3];
 #pragma unroll
@@ -306,14 +318,15 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
     int k = 0;
     for (int kz = u.kz0; kz < u.kz1; ++kz) {
         const int z0 = kz * d.dz, zn = imin(d.dz, d.Z - z0);
-        for (int rz = 0; rz < zn; ++rz) {
+        for (int rz = 0; rz < zn; ++rz, gz += plane_pitch) {
             float hy[4][3];
 #pragma unroll
             for (int m = 0; m < 4; ++m)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) hy[m][c] = 0.f;
 
-            for (int ry = 0; ry < yn; ++ry, ++k) {
+            uintptr_t g = gz;
+            for (int ry = 0; ry < yn; ++ry, ++k, g += row_pitch) {
                 const unsigned qq = q0 + (unsigned)k;
                 const unsigned st = qq % kLoadStages;
                 if (!mbar_wait_bounded(&bars[st], (qq / kLoadStages) & 1u)) {
@@ -327,15 +340,15 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
                     q = q0 + (unsigned)rows;
                     return false;
                 }
-                const long long e0 = field_elem(d, z0 + rz, y0 + ry, u.xs);
-                const RowLoad L = row_load(gbase + 4 * e0, nbytes, A0, A1);
-                unsigned char* sb = bufs + st * buf_bytes + (L.g - L.lo);
-                BSI_GUARD((int)(L.g - L.lo) + nbytes <= buf_bytes && e0 + 3LL * u.nvox <= 3LL * d.X * d.Y * d.Z,
+                unsigned char* sb = bufs + st * buf_bytes + (g & 15);
+                BSI_GUARD((int)(g & 15) + nbytes <= buf_bytes && g >= gbase &&
+                              (long long)(g - gbase) / 4 + 3LL * u.nvox <= 3LL * d.X * d.Y * d.Z,
                           kErrGradRead, err) {
-                    if (L.g < L.s0 || L.g + (uintptr_t)nbytes > L.s1) {
+                    if (g < A0 || g + (uintptr_t)nbytes > A1) {
                         // first or last row of the array: elements outside the bulk copy
+                        const RowLoad L = row_load(reinterpret_cast<const unsigned char*>(g), nbytes, A0, A1);
                         for (int i = lane; i < u.nvox * 3; i += kLanes) {
-                            const uintptr_t a = L.g + 4u * (uintptr_t)i;
+                            const uintptr_t a = g + 4u * (uintptr_t)i;
                             if (a < L.s0 || a >= L.s1)
                                 reinterpret_cast<float*>(sb)[i] = *reinterpret_cast<const float*>(a);
                         }
@@ -358,7 +371,7 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
                 // this ring buffer may be refilled once every lane has read it
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0 && k + kLoadStages < rows) issue(k + kLoadStages);
+                if (lane == 0 && ik < rows) issue_next();
 
                 // column sum: the column of lane l collects q4[k] of the tile k lanes below
                 const float b0 = c_lut.w[wyb + 4 * ry], b1 = c_lut.w[wyb + 4 * ry + 1];
