@@ -93,7 +93,7 @@ static bsi_status check_geom(const bsi_geom* g) {
 
 static bool empty_volume(const bsi_geom& g) { return g.X == 0 || g.Y == 0 || g.Z == 0; }
 
-static void fill_desc(InstDesc& d, const bsi_geom& g, bool adjoint, int zchunk) {
+static void fill_desc(InstDesc& d, const bsi_geom& g, bool adjoint, int zchunk, bool bf16 = false) {
     std::memset(&d, 0, sizeof d);
     d.X = (int)g.X;
     d.Y = (int)g.Y;
@@ -111,7 +111,8 @@ static void fill_desc(InstDesc& d, const bsi_geom& g, bool adjoint, int zchunk) 
         d.ncz = (int)cdiv(g.Z, g.dz);
     }
     if (!adjoint) {
-        d.nxg = empty ? 0 : (int)cdiv(d.ncx, kGroupCells);
+        d.gcells = fwd_strip_tiles(d.X, d.dx, bf16);
+        d.nxg = empty ? 0 : (int)cdiv(d.ncx, d.gcells);
         d.units = (long long)d.ncz * d.ncy * d.nxg;
     } else {
         d.zchunk = zchunk;
@@ -223,10 +224,10 @@ static bsi_status check_instances(const bsi_instance* inst, int n, bool fwd, boo
     return BSI_OK;
 }
 
-static std::vector<InstDesc> descs(const bsi_instance* inst, int n, bool adjoint) {
+static std::vector<InstDesc> descs(const bsi_instance* inst, int n, bool adjoint, bool bf16 = false) {
     std::vector<InstDesc> v((size_t)n);
     for (int i = 0; i < n; ++i) {
-        fill_desc(v[(size_t)i], inst[i].geom, adjoint, kDefaultZChunk);
+        fill_desc(v[(size_t)i], inst[i].geom, adjoint, kDefaultZChunk, bf16);
         v[(size_t)i].phi = inst[i].phi;
         v[(size_t)i].field = inst[i].field;
         v[(size_t)i].grad = inst[i].grad_field;
@@ -239,7 +240,7 @@ static bsi_status forward_impl(const bsi_instance* inst, int n, bsi_dtype dt, cu
     if (dt != BSI_F32 && dt != BSI_BF16) return BSI_ERR_DTYPE;
     bsi_status st = check_instances(inst, n, true, false, dt);
     if (st != BSI_OK) return st;
-    std::vector<InstDesc> all = descs(inst, n, false);
+    std::vector<InstDesc> all = descs(inst, n, false, dt == BSI_BF16);
     all.erase(std::remove_if(all.begin(), all.end(), [](const InstDesc& d) { return d.units == 0; }), all.end());
     for (const Group& g : plan(all, nullptr)) {
         const cudaError_t e = run_group(g, Op::Forward, dt == BSI_BF16, nullptr, 0, s);
@@ -512,7 +513,7 @@ int bsi_selfcheck_ranges(const bsi_instance* inst, int n, int op, int cover, cha
         if (!ok) {
             rc.fail("invalid geometry", n, 0);
         } else if (op < 2) {
-            std::vector<InstDesc> all = descs(inst, n, false);
+            std::vector<InstDesc> all = descs(inst, n, false, op == 1);
             all.erase(std::remove_if(all.begin(), all.end(), [](const InstDesc& d) { return d.units == 0; }),
                       all.end());
             for (const Group& g : plan(all, nullptr)) check_forward_group(g, op == 1 ? 2 : 4, rc, cover != 0);

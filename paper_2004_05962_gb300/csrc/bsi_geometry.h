@@ -41,7 +41,7 @@ struct InstDesc {
     int nxg;             // x-groups: ceil(ncx/29) forward, ceil(nx/29) adjoint
     int nzc;             // adjoint: tile-plane chunks
     int zchunk;          // adjoint: tile-planes per chunk
-    int reserved;
+    int gcells;          // forward: tiles per warp strip (<= 29; see fwd_strip_tiles)
     long long units;        // units of this instance
     long long unit_begin;   // first global unit index of this instance in its launch
     long long point_begin;  // adjoint reduce: first global grid point of this instance
@@ -89,14 +89,23 @@ struct FwdUnit {
     int nvox;    // voxels per row of the strip
 };
 
+// Tiles per forward strip.  With FP32 output and X a multiple of 4, a strip
+// whose first voxel is a multiple of 4 starts every row segment on a 16-byte
+// boundary (12 bytes per voxel), so each row leaves as one aligned bulk copy
+// with no unaligned head or tail: 28 tiles when dx is not a multiple of 4
+// (28 dx = 0 mod 4), else all 29.  Otherwise rows are unaligned anyway: 29.
+BSI_HD int fwd_strip_tiles(int X, int dx, bool bf16) {
+    return (!bf16 && X % 4 == 0 && dx % 4 != 0) ? kGroupCells - 1 : kGroupCells;
+}
+
 BSI_HD FwdUnit fwd_unit(const InstDesc& d, long long ul) {
     FwdUnit u;
     u.xg = (int)(ul % d.nxg);
     const long long t = ul / d.nxg;
     u.jy = (int)(t % d.ncy);
     u.kz = (int)(t / d.ncy);
-    u.cell0 = u.xg * kGroupCells;
-    u.ncell = imin(kGroupCells, d.ncx - u.cell0);
+    u.cell0 = u.xg * d.gcells;
+    u.ncell = imin(d.gcells, d.ncx - u.cell0);
     u.x0 = u.cell0 * d.dx;
     u.nvox = imin(u.ncell * d.dx, d.X - u.x0);
     return u;

@@ -88,6 +88,14 @@ __device__ __forceinline__ void put3(unsigned char* s, int e, float a, float b, 
 template <int ES>
 __device__ __forceinline__ void store_row(const unsigned char* sb, unsigned char* g, int shift, int nbytes,
                                           int lane) {
+    if (shift == 0 && (nbytes & 15) == 0) {  // aligned segment (warp-uniform): one bulk copy, no ends
+        if (lane == 0) {
+            bulk_store(g, sb, (uint32_t)nbytes);
+            bulk_commit();
+            bulk_wait_read<kStoreStages - 1>();
+        }
+        return;
+    }
     int head = (16 - shift) & 15;
     head = head < nbytes ? head : nbytes;
     const int body = (nbytes - head) & ~15;
