@@ -176,7 +176,7 @@ template <int MAXB>
 static void to_batch(const Group& g, Batch<MAXB>& b) {
     std::memset(&b, 0, sizeof b);
     b.n = (int)g.inst.size();
-    b.buf_bytes = stage_buf_bytes(g.generic ? g.dxmax : kMaxSpecializedDx);
+    b.buf_bytes = stage_buf_bytes(g.dxmax);
     for (int i = 0; i < b.n; ++i) {
         b.inst[i] = g.inst[i];
         b.total_units += g.inst[i].units;
@@ -285,7 +285,7 @@ struct RangeChecker {
 // staging copy fits its shared-memory buffer, and (when `cover` is set) that
 // the rows of the units tile the field exactly once.
 static void check_forward_group(const Group& g, int es, RangeChecker& rc, bool cover) {
-    const int buf = stage_buf_bytes(g.generic ? g.dxmax : kMaxSpecializedDx);
+    const int buf = stage_buf_bytes(g.dxmax);
     for (const InstDesc& d : g.inst) {
         const long long phi_elems = 3LL * d.nx * d.ny * d.nz;
         const long long field_elems = 3LL * d.X * d.Y * d.Z;
@@ -326,7 +326,7 @@ static void check_forward_group(const Group& g, int es, RangeChecker& rc, bool c
 }
 
 static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecker& rc, bool cover) {
-    const int buf = stage_buf_bytes(g.generic ? g.dxmax : kMaxSpecializedDx);
+    const int buf = stage_buf_bytes(g.dxmax);
     std::vector<unsigned char> written(cover ? (size_t)(ws_floats / 3 + 1) : 0, 0);
     for (const InstDesc& d : g.inst) {
         const long long field_elems = 3LL * d.X * d.Y * d.Z;
