@@ -356,6 +356,15 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
         P.bsi_field_forward_batched(phis, shapes, spacings, outs=outs)
         P.bsi_field_adjoint_batched(grads, spacings, outs=dps, workspace=bws)
 
+    # untuned (library defaults), then autotuned launch shapes per spacing class
+    from paper_2004_05962_gb300 import tune
+
+    t_default = time_fn(bstep, s, 10)
+    t_tune0 = time.time()
+    tuned = tune.tune_batched(shapes, spacings, iters=5)
+    tune_s = time.time() - t_tune0
+    bws = torch.empty(P.bsi_batched_adjoint_workspace_bytes(shapes, spacings), dtype=torch.uint8, device=dev)
+
     side = torch.cuda.Stream(dev)
     side.wait_stream(s)
     with torch.cuda.stream(side):
@@ -370,7 +379,12 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
     res["batched_64"] = {"gvox_s_fwd_adj": round(bvox / tb / 1e6, 2), "ms_fwd_adj": round(tb, 5),
                          "gvox_s_fwd": round(bvox / tbf / 1e6, 2), "voxels": bvox,
                          "vs_single_volume_fwd": round((bvox / tbf) / (nvox / ms), 3),
-                         "launches_per_step": 3, "cuda_graph": True}
+                         "vs_single_volume_fwd_adj": round((bvox / tb) / (nvox / (ms + msa)), 3),
+                         "launches_per_step": 3, "cuda_graph": True,
+                         "autotuned": {k: v for k, v in tuned.items() if k not in ("dx", "dy", "dz")},
+                         "spacing_classes": len(set(map(tuple, spacings))),
+                         "tuning_s": round(tune_s, 1), "gvox_s_fwd_adj_untuned": round(bvox / t_default / 1e6, 2)}
+    P.bsi_set_tile_configs([])
     del phis, grads, outs, dps, bws, g
 
     # end to end through the public API with host buffers: H2D of phi and the voxel

@@ -163,6 +163,34 @@ bsi_status bsi_field_adjoint_batched(const bsi_instance* inst, int n, void* work
 bsi_status bsi_field_adjoint_noalloc(const bsi_geom* g, const float* grad_field, float* grad_phi,
                                      bsi_stream_t stream);
 
+/* Launch shape for one spacing class, chosen by the autotuner
+ * (paper_2004_05962_gb300/tune.py times candidates and keeps a JSON cache).
+ * The paper tunes its block shape per GPU by hand (Sec. 3.4); here the shape
+ * is data.  A zero field means "library default". */
+typedef struct {
+    int32_t dx, dy, dz;        /* spacing the entry applies to; 0 matches any value */
+    int32_t adj_zchunk;        /* adjoint: tile-planes per warp unit, 3..16 (default 4) */
+    int32_t adj_warps;         /* adjoint: warps per CTA, 1..8 (default 8, fewer if shared
+                                  memory requires) */
+    int32_t fwd_strip_tiles;   /* forward: tiles per warp strip, 4..29 (default 28 or 29,
+                                  whichever keeps FP32 rows 16-byte aligned) */
+    int32_t fwd_warps;         /* forward: warps per CTA, 1..8 (default as adj_warps) */
+} bsi_tile_config;
+
+#define BSI_MAX_TILE_CONFIGS 256
+
+/* Replaces the process-wide table (host memory, copied; n = 0 clears it).
+ * Every later call plans with it: an instance takes the first entry whose
+ * non-zero dx/dy/dz all match its spacing.  Because adj_zchunk changes the
+ * adjoint workspace size, query the workspace after setting the table.
+ * Returns BSI_ERR_BATCH for n outside 0..BSI_MAX_TILE_CONFIGS, BSI_ERR_SPACING
+ * for a field out of range (the table is then left unchanged). */
+bsi_status bsi_set_tile_configs(const bsi_tile_config* cfgs, int n);
+
+/* The launch shape the library will use for spacing (dx, dy, dz), defaults
+ * filled in; BSI_ERR_NULL if out is NULL, BSI_ERR_SPACING for a bad spacing. */
+bsi_status bsi_get_tile_config(int32_t dx, int32_t dy, int32_t dz, bsi_tile_config* out);
+
 /* Static string naming a status code. */
 const char* bsi_status_string(bsi_status s);
 

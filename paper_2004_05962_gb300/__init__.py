@@ -14,7 +14,11 @@ from .bsi import (  # noqa: F401
     bsi_field_adjoint_batched,
     bsi_field_forward,
     bsi_field_forward_batched,
+    bsi_field_adjoint_noalloc,
+    bsi_get_tile_config,
     bsi_selfcheck_ranges,
+    bsi_set_tile_configs,
+    bsi_tile_configs,
     grid_shape,
     library,
 )

@@ -53,6 +53,17 @@ class BsiInstance(ctypes.Structure):
                 ("grad_field", ctypes.c_void_p), ("grad_phi", ctypes.c_void_p)]
 
 
+class BsiTileConfig(ctypes.Structure):
+    _fields_ = [("dx", ctypes.c_int32), ("dy", ctypes.c_int32), ("dz", ctypes.c_int32),
+                ("adj_zchunk", ctypes.c_int32), ("adj_warps", ctypes.c_int32),
+                ("fwd_strip_tiles", ctypes.c_int32), ("fwd_warps", ctypes.c_int32)]
+
+    FIELDS = ("dx", "dy", "dz", "adj_zchunk", "adj_warps", "fwd_strip_tiles", "fwd_warps")
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k in self.FIELDS}
+
+
 _LIBS: dict = {}
 _USE_CHECKED = os.environ.get("BSI_CHECKED", "0") == "1"
 
@@ -96,6 +107,9 @@ def library(checked: bool | None = None) -> ctypes.CDLL:
         "bsi_version": (i32, []),
         "bsi_selfcheck_ranges": (i32, [I, i32, i32, i32, ctypes.c_char_p, sz]),
         "bsi_field_adjoint_noalloc": (i32, [G, vp, vp, vp]),
+        "bsi_set_tile_configs": (i32, [ctypes.POINTER(BsiTileConfig), i32]),
+        "bsi_get_tile_config": (i32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(BsiTileConfig)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -110,7 +124,36 @@ def exported_symbols():
             "bsi_field_forward_batched", "bsi_batched_adjoint_workspace_bytes",
             "bsi_field_adjoint_batched", "bsi_status_string", "bsi_last_cuda_error",
             "bsi_check_device_status", "bsi_version", "bsi_selfcheck_ranges",
-            "bsi_field_adjoint_noalloc"]
+            "bsi_field_adjoint_noalloc", "bsi_set_tile_configs", "bsi_get_tile_config"]
+
+
+def bsi_set_tile_configs(configs) -> None:
+    """Replaces the library's launch-shape table with ``configs`` (a list of dicts
+    with keys dx, dy, dz, adj_zchunk, adj_warps, fwd_strip_tiles, fwd_warps;
+    missing keys are 0 = default / wildcard)."""
+    global _TILE_TABLE
+    arr = (BsiTileConfig * max(1, len(configs)))()
+    for i, c in enumerate(configs):
+        for k in BsiTileConfig.FIELDS:
+            setattr(arr[i], k, int(c.get(k, 0)))
+    _check(library().bsi_set_tile_configs(arr, len(configs)), "bsi_set_tile_configs")
+    _TILE_TABLE = [{k: int(c.get(k, 0)) for k in BsiTileConfig.FIELDS} for c in configs]
+
+
+_TILE_TABLE: list = []
+
+
+def bsi_tile_configs() -> list:
+    """The table last installed through this module (a copy)."""
+    return [dict(c) for c in _TILE_TABLE]
+
+
+def bsi_get_tile_config(spacing) -> dict:
+    """The launch shape the library uses for spacing (dz, dy, dx)."""
+    dz, dy, dx = (int(s) for s in spacing)
+    c = BsiTileConfig()
+    _check(library().bsi_get_tile_config(dx, dy, dz, ctypes.byref(c)), "bsi_get_tile_config")
+    return c.as_dict()
 
 
 # ---------------------------------------------------------------- helpers

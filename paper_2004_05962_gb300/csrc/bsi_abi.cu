@@ -93,8 +93,35 @@ static bsi_status check_geom(const bsi_geom* g) {
 
 static bool empty_volume(const bsi_geom& g) { return g.X == 0 || g.Y == 0 || g.Z == 0; }
 
-static void fill_desc(InstDesc& d, const bsi_geom& g, bool adjoint, int zchunk, bool bf16 = false) {
+// ----------------------------------------------------------- tile-config table
+
+static std::mutex g_cfg_mu;
+static std::vector<bsi_tile_config> g_cfg;
+
+static bool config_valid(const bsi_tile_config& c) {
+    auto sp = [](int32_t v) { return v == 0 || (v >= 1 && v <= BSI_MAX_SPACING); };
+    return sp(c.dx) && sp(c.dy) && sp(c.dz) && (c.adj_zchunk == 0 || (c.adj_zchunk >= 3 && c.adj_zchunk <= 16)) &&
+           (c.fwd_strip_tiles == 0 || (c.fwd_strip_tiles >= 4 && c.fwd_strip_tiles <= kGroupCells)) &&
+           (c.adj_warps >= 0 && c.adj_warps <= kMaxWarpsPerCta) &&
+           (c.fwd_warps >= 0 && c.fwd_warps <= kMaxWarpsPerCta);
+}
+
+// The table entry for spacing (dx, dy, dz) with zero fields left as they are
+// (the caller applies the defaults), or an all-zero config if none matches.
+static bsi_tile_config lookup_config(int32_t dx, int32_t dy, int32_t dz) {
+    std::lock_guard<std::mutex> lk(g_cfg_mu);
+    for (const bsi_tile_config& c : g_cfg)
+        if ((c.dx == 0 || c.dx == dx) && (c.dy == 0 || c.dy == dy) && (c.dz == 0 || c.dz == dz)) return c;
+    bsi_tile_config z;
+    std::memset(&z, 0, sizeof z);
+    return z;
+}
+
+static void fill_desc(InstDesc& d, const bsi_geom& g, bool adjoint, bool bf16 = false) {
+    const bsi_tile_config cfg = lookup_config(g.dx, g.dy, g.dz);
+    const int zchunk = cfg.adj_zchunk > 0 ? cfg.adj_zchunk : kDefaultZChunk;
     std::memset(&d, 0, sizeof d);
+    d.warps_req = adjoint ? cfg.adj_warps : cfg.fwd_warps;
     d.X = (int)g.X;
     d.Y = (int)g.Y;
     d.Z = (int)g.Z;
@@ -111,7 +138,7 @@ static void fill_desc(InstDesc& d, const bsi_geom& g, bool adjoint, int zchunk, 
         d.ncz = (int)cdiv(g.Z, g.dz);
     }
     if (!adjoint) {
-        d.gcells = fwd_strip_tiles(d.X, d.dx, bf16);
+        d.gcells = cfg.fwd_strip_tiles > 0 ? cfg.fwd_strip_tiles : fwd_strip_tiles(d.X, d.dx, bf16);
         d.nxg = empty ? 0 : (int)cdiv(d.ncx, d.gcells);
         d.units = (long long)d.ncz * d.ncy * d.nxg;
     } else {
@@ -131,6 +158,7 @@ static long long adj_floats(const InstDesc& d) {
 struct Group {
     bool generic = false;
     int dxmax = 1;
+    int warps_req = 0;   // smallest non-zero warps_per_cta request of its instances
     std::vector<InstDesc> inst;
 };
 
@@ -151,10 +179,12 @@ static std::vector<Group> plan(const std::vector<InstDesc>& all, long long* ws_f
             off += adj_floats(d);
             cur.inst.push_back(d);
             cur.dxmax = std::max(cur.dxmax, d.dx);
+            if (d.warps_req > 0 && (cur.warps_req == 0 || d.warps_req < cur.warps_req)) cur.warps_req = d.warps_req;
             if ((int)cur.inst.size() == kMaxBatch) {
                 out.push_back(cur);
                 cur.inst.clear();
                 cur.dxmax = 1;
+                cur.warps_req = 0;
             }
         }
         if (!cur.inst.empty()) out.push_back(cur);
@@ -177,6 +207,7 @@ static void to_batch(const Group& g, Batch<MAXB>& b) {
     std::memset(&b, 0, sizeof b);
     b.n = (int)g.inst.size();
     b.buf_bytes = stage_buf_bytes(g.dxmax);
+    b.warps_req = g.warps_req;
     for (int i = 0; i < b.n; ++i) {
         b.inst[i] = g.inst[i];
         b.total_units += g.inst[i].units;
@@ -227,7 +258,7 @@ static bsi_status check_instances(const bsi_instance* inst, int n, bool fwd, boo
 static std::vector<InstDesc> descs(const bsi_instance* inst, int n, bool adjoint, bool bf16 = false) {
     std::vector<InstDesc> v((size_t)n);
     for (int i = 0; i < n; ++i) {
-        fill_desc(v[(size_t)i], inst[i].geom, adjoint, kDefaultZChunk, bf16);
+        fill_desc(v[(size_t)i], inst[i].geom, adjoint, bf16);
         v[(size_t)i].phi = inst[i].phi;
         v[(size_t)i].field = inst[i].field;
         v[(size_t)i].grad = inst[i].grad_field;
@@ -427,7 +458,7 @@ bsi_status bsi_field_forward(const bsi_geom* g, const float* phi, void* field, b
 size_t bsi_adjoint_workspace_bytes(const bsi_geom* g) {
     if (check_geom(g) != BSI_OK) return 0;
     InstDesc d;
-    fill_desc(d, *g, true, kDefaultZChunk);
+    fill_desc(d, *g, true);
     return (size_t)adj_floats(d) * sizeof(float);
 }
 
@@ -452,7 +483,7 @@ size_t bsi_batched_adjoint_workspace_bytes(const bsi_instance* inst, int n) {
     for (int i = 0; i < n; ++i) {
         if (check_geom(&inst[i].geom) != BSI_OK) return 0;
         InstDesc d;
-        fill_desc(d, inst[i].geom, true, kDefaultZChunk);
+        fill_desc(d, inst[i].geom, true);
         total += adj_floats(d);
     }
     return (size_t)total * sizeof(float);
@@ -482,6 +513,31 @@ const char* bsi_status_string(bsi_status s) {
 }
 
 const char* bsi_last_cuda_error(void) { return t_cuda_msg; }
+
+bsi_status bsi_set_tile_configs(const bsi_tile_config* cfgs, int n) {
+    if (n < 0 || n > BSI_MAX_TILE_CONFIGS || (n > 0 && !cfgs)) return BSI_ERR_BATCH;
+    for (int i = 0; i < n; ++i)
+        if (!config_valid(cfgs[i])) return BSI_ERR_SPACING;
+    std::lock_guard<std::mutex> lk(g_cfg_mu);
+    g_cfg.assign(cfgs, cfgs + n);
+    return BSI_OK;
+}
+
+bsi_status bsi_get_tile_config(int32_t dx, int32_t dy, int32_t dz, bsi_tile_config* out) {
+    if (!out) return BSI_ERR_NULL;
+    if (dx < 1 || dy < 1 || dz < 1 || dx > BSI_MAX_SPACING || dy > BSI_MAX_SPACING || dz > BSI_MAX_SPACING)
+        return BSI_ERR_SPACING;
+    bsi_tile_config c = lookup_config(dx, dy, dz);
+    c.dx = dx;
+    c.dy = dy;
+    c.dz = dz;
+    if (c.adj_zchunk == 0) c.adj_zchunk = kDefaultZChunk;
+    if (c.adj_warps == 0) c.adj_warps = kMaxWarpsPerCta;
+    if (c.fwd_warps == 0) c.fwd_warps = kMaxWarpsPerCta;
+    // fwd_strip_tiles stays 0 when unset: it then depends on the volume (X % 4) and dtype
+    *out = c;
+    return BSI_OK;
+}
 
 bsi_status bsi_check_device_status(bsi_stream_t stream, uint32_t* flags) {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -131,7 +131,7 @@ template <int MAXB, bool GENERIC>
 static cudaError_t launch_part_t(const Batch<MAXB>& b, float* part, long long ws_floats, cudaStream_t s,
                                  LaunchInfo* info) {
     auto kern = bsi_adjoint_partials_kernel<MAXB, GENERIC>;
-    const int wpc = warps_per_cta(adj_warp_smem(b.buf_bytes));
+    const int wpc = warps_per_cta(adj_warp_smem(b.buf_bytes), b.warps_req);
     const int threads = wpc * kLanes;
     const int smem = wpc * adj_warp_smem(b.buf_bytes);
     KernelFacts f;

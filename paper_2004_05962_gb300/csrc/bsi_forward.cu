@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
 template <int MAXB, bool BF16, bool GENERIC>
 static cudaError_t launch_fwd_t(const Batch<MAXB>& b, cudaStream_t s, LaunchInfo* info) {
     auto kern = bsi_forward_kernel<MAXB, BF16, GENERIC>;
-    const int wpc = warps_per_cta(fwd_warp_smem(b.buf_bytes));
+    const int wpc = warps_per_cta(fwd_warp_smem(b.buf_bytes), b.warps_req);
     const int threads = wpc * kLanes;
     const int smem = wpc * fwd_warp_smem(b.buf_bytes);
     KernelFacts f;

@@ -42,6 +42,8 @@ struct InstDesc {
     int nzc;             // adjoint: tile-plane chunks
     int zchunk;          // adjoint: tile-planes per chunk
     int gcells;          // forward: tiles per warp strip (<= 29; see fwd_strip_tiles)
+    int warps_req;       // requested warps per CTA from the tile-config table (0: automatic)
+    int reserved;
     long long units;        // units of this instance
     long long unit_begin;   // first global unit index of this instance in its launch
     long long point_begin;  // adjoint reduce: first global grid point of this instance
@@ -55,7 +57,9 @@ struct InstDesc {
 template <int MAXB>
 struct Batch {
     int n;
-    int buf_bytes;          // bytes of ONE per-warp staging buffer (two per warp)
+    int buf_bytes;          // bytes of one staging row slot (stage_buf_bytes of the largest dx)
+    int warps_req;          // requested warps per CTA (0: as many as shared memory allows, <= 8)
+    int reserved;
     long long total_units;
     long long total_points;
     InstDesc inst[MAXB];
@@ -167,9 +171,11 @@ BSI_HD int adj_warp_smem(int buf_bytes) { return kLoadStages * (16 + buf_bytes);
 constexpr int kMaxWarpsPerCta = 8;
 constexpr int kSmemBudget = 200 * 1024;   // dynamic shared memory per CTA we allow
 
-// Warps per CTA such that the warps' shared memory fits the budget.
-BSI_HD int warps_per_cta(int warp_smem) {
-    const int w = kSmemBudget / warp_smem;
+// Warps per CTA such that the warps' shared memory fits the budget, at most
+// `req` when a tile config asks for fewer (req = 0: no request).
+BSI_HD int warps_per_cta(int warp_smem, int req = 0) {
+    int w = kSmemBudget / warp_smem;
+    if (req > 0 && req < w) w = req;
     return w < 1 ? 1 : (w > kMaxWarpsPerCta ? kMaxWarpsPerCta : w);
 }
 
