@@ -112,14 +112,17 @@ __device__ __forceinline__ void store_row(const unsigned char* sb, unsigned char
     }
 }
 
-// x-stage of one voxel of a tile: out = sum_l B_l(r/dx) p_l, per channel.
+// x-stage of one voxel of a tile: out = sum_l B_l(r/dx) p_l, per channel.  A
+// voxel outside the strip (on == false) is computed but not stored.
 template <bool BF16>
 __device__ __forceinline__ void emit_voxel(unsigned char* sb, int e, int wo, const float (&p0)[3],
-                                           const float (&p1)[3], const float (&p2)[3], const float (&p3)[3]) {
+                                           const float (&p1)[3], const float (&p2)[3], const float (&p3)[3],
+                                           bool on) {
     const float w0 = c_lut.w[wo], w1 = c_lut.w[wo + 1], w2 = c_lut.w[wo + 2], w3 = c_lut.w[wo + 3];
-    put3<BF16>(sb, e, fmaf(w3, p3[0], fmaf(w2, p2[0], fmaf(w1, p1[0], w0 * p0[0]))),
-               fmaf(w3, p3[1], fmaf(w2, p2[1], fmaf(w1, p1[1], w0 * p0[1]))),
-               fmaf(w3, p3[2], fmaf(w2, p2[2], fmaf(w1, p1[2], w0 * p0[2]))));
+    const float v0 = fmaf(w3, p3[0], fmaf(w2, p2[0], fmaf(w1, p1[0], w0 * p0[0])));
+    const float v1 = fmaf(w3, p3[1], fmaf(w2, p2[1], fmaf(w1, p1[1], w0 * p0[1])));
+    const float v2 = fmaf(w3, p3[2], fmaf(w2, p2[2], fmaf(w1, p1[2], w0 * p0[2])));
+    if (on) put3<BF16>(sb, e, v0, v1, v2);
 }
 
 // One forward unit: tile-plane kz, tile-row jy, x-group xg.  DX > 0 is a
@@ -159,8 +162,8 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
     const int y0 = u.jy * d.dy, yn = imin(d.dy, d.Y - y0);
     const int wzb = weight_base(d.dz), wyb = weight_base(d.dy), wxb = weight_base(dx);
     const int xl = lane * dx;                 // first strip voxel of this lane's tile
-    const bool emits = lane < u.ncell;
-    const bool full = emits && xl + dx <= u.nvox;
+    // voxels of this lane's tile inside the strip (0 for the halo lanes)
+    const int rn = lane < u.ncell ? imin(dx, u.nvox - xl) : 0;
     const int nbytes = u.nvox * 3 * ES;
     const long long row_pitch = 3LL * d.X * ES;          // bytes from row y to row y + 1
     const long long plane_pitch = row_pitch * d.Y;       // bytes from plane z to plane z + 1
@@ -194,13 +197,14 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
             ring = ring == kStoreStages - 1 ? 0 : ring + 1;
             // (the ring buffer is free: store_row of the previous row waited for it)
             BSI_GUARD(shift + nbytes <= buf_bytes, kErrStage, err) {
-                if (DX > 0 && full) {
+                if (DX > 0) {  // one predicated path for all lanes: full, cut and halo tiles
 #pragma unroll
                     for (int r = 0; r < (DX > 0 ? DX : 1); ++r)
-                        emit_voxel<BF16>(sb, (xl + r) * 3, weight_base(DX > 0 ? DX : 1) + 4 * r, p0, p1, p2, p3);
-                } else if (emits) {  // run-time spacing, or the tile cut by the volume's x-end
-                    const int rn = imin(dx, u.nvox - xl);
-                    for (int r = 0; r < rn; ++r) emit_voxel<BF16>(sb, (xl + r) * 3, wxb + 4 * r, p0, p1, p2, p3);
+                        emit_voxel<BF16>(sb, (xl + r) * 3, weight_base(DX > 0 ? DX : 1) + 4 * r, p0, p1, p2, p3,
+                                         r < rn);
+                } else {
+                    for (int r = 0; r < rn; ++r)
+                        emit_voxel<BF16>(sb, (xl + r) * 3, wxb + 4 * r, p0, p1, p2, p3, true);
                 }
             }
             fence_proxy_async_smem();  // this lane's staging writes before the bulk copy reads them
@@ -256,9 +260,15 @@ __device__ __forceinline__ RowLoad row_load(const unsigned char* g, int nbytes, 
     return r;
 }
 
-// x-transpose of one voxel: q_l += B_l(r/dx) g, per channel.
-__device__ __forceinline__ void gather_voxel(float (&q4)[4][3], const float* sv, int wo) {
-    const float g0 = sv[0], g1 = sv[1], g2 = sv[2];
+// x-transpose of one voxel: q_l += B_l(r/dx) g, per channel; a voxel outside
+// the volume (on == false) contributes nothing and is not read.
+__device__ __forceinline__ void gather_voxel(float (&q4)[4][3], const float* sv, int wo, bool on) {
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (on) {
+        g0 = sv[0];
+        g1 = sv[1];
+        g2 = sv[2];
+    }
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
         const float w = c_lut.w[wo + l];
@@ -288,6 +298,9 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
     const uintptr_t A0 = ceil16(gbase);
     const uintptr_t A1 = floor16(gbase + (uintptr_t)(12LL * d.X * d.Y * d.Z));
     const uintptr_t g_first = gbase + 4 * field_elem(d, zb, y0, u.xs);   // row 0 of the unit
+    // only a unit holding the first or last row of the array has bytes outside the bulk copies
+    const bool unit_edge = g_first < A0 ||
+        gbase + 4 * field_elem(d, imin(u.kz1 * d.dz, d.Z) - 1, y0 + yn - 1, u.xs) + (uintptr_t)nbytes > A1;
     const unsigned q0 = q;
 
     // Producer (lane 0): puts the unit's rows in flight in order, row k into ring
@@ -352,7 +365,7 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
                 BSI_GUARD((int)(g & 15) + nbytes <= buf_bytes && g >= gbase &&
                               (long long)(g - gbase) / 4 + 3LL * u.nvox <= 3LL * d.X * d.Y * d.Z,
                           kErrGradRead, err) {
-                    if (g < A0 || g + (uintptr_t)nbytes > A1) {
+                    if (unit_edge && (g < A0 || g + (uintptr_t)nbytes > A1)) {
                         // first or last row of the array: elements outside the bulk copy
                         const RowLoad L = row_load(reinterpret_cast<const unsigned char*>(g), nbytes, A0, A1);
                         for (int i = lane; i < u.nvox * 3; i += kLanes) {
@@ -369,12 +382,12 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
                 for (int l = 0; l < 4; ++l)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) q4[l][c] = 0.f;
-                if (DX > 0 && nv == DX) {
+                if (DX > 0) {  // one predicated path for all lanes: full, cut and empty tiles
 #pragma unroll
                     for (int r = 0; r < (DX > 0 ? DX : 1); ++r)
-                        gather_voxel(q4, sv + 3 * r, weight_base(DX > 0 ? DX : 1) + 4 * r);
+                        gather_voxel(q4, sv + 3 * r, weight_base(DX > 0 ? DX : 1) + 4 * r, r < nv);
                 } else {
-                    for (int r = 0; r < nv; ++r) gather_voxel(q4, sv + 3 * r, wxb + 4 * r);
+                    for (int r = 0; r < nv; ++r) gather_voxel(q4, sv + 3 * r, wxb + 4 * r, true);
                 }
                 // this ring buffer may be refilled once every lane has read it
                 fence_proxy_async_smem();
