@@ -311,6 +311,39 @@ struct RangeChecker {
     }
 };
 
+// Checks that slot_unit hands every unit of a launch to exactly one slot, for
+// a spread of grid shapes (the actual grid depends on the device), and that
+// each slot's units increase (the kernels scan instances forward).
+static void check_slots(long long total, RangeChecker& rc) {
+    const int ctas_list[] = {1, 3, 152, 304, 1000};
+    const int wpc_list[] = {1, 5, 8};
+    std::vector<unsigned char> seen((size_t)total, 0);
+    for (int spread = 0; spread < 2; ++spread)
+    for (int ctas : ctas_list)
+        for (int wpc : wpc_list) {
+            std::fill(seen.begin(), seen.end(), 0);
+            for (int c = 0; c < ctas; ++c)
+                for (int w = 0; w < wpc; ++w) {
+                    long long prev = -1;
+                    for (long long r = 0;; ++r) {
+                        const long long u = slot_unit(r, c, w, ctas, wpc, total, spread != 0);
+                        if (u < 0) break;
+                        if (u >= total || u <= prev) {
+                            rc.fail("slot order", u, prev);
+                            break;
+                        }
+                        seen[(size_t)u]++;
+                        prev = u;
+                    }
+                }
+            for (long long u = 0; u < total; ++u)
+                if (seen[(size_t)u] != 1) {
+                    rc.fail("unit not taken exactly once", u, ctas * 100 + wpc);
+                    break;
+                }
+        }
+}
+
 // Walks every unit of a forward launch plan and checks, with the kernels' own
 // index functions, that each read and write lies inside its buffer, that each
 // staging copy fits its shared-memory buffer, and (when `cover` is set) that
@@ -572,11 +605,21 @@ int bsi_selfcheck_ranges(const bsi_instance* inst, int n, int op, int cover, cha
             std::vector<InstDesc> all = descs(inst, n, false, op == 1);
             all.erase(std::remove_if(all.begin(), all.end(), [](const InstDesc& d) { return d.units == 0; }),
                       all.end());
-            for (const Group& g : plan(all, nullptr)) check_forward_group(g, op == 1 ? 2 : 4, rc, cover != 0);
+            for (const Group& g : plan(all, nullptr)) {
+                check_forward_group(g, op == 1 ? 2 : 4, rc, cover != 0);
+                long long total = 0;
+                for (const InstDesc& d : g.inst) total += d.units;
+                if (cover) check_slots(total, rc);
+            }
         } else {
             long long ws = 0;
             const std::vector<Group> groups = plan(descs(inst, n, true), &ws);
-            for (const Group& g : groups) check_adjoint_group(g, ws, rc, cover != 0);
+            for (const Group& g : groups) {
+                check_adjoint_group(g, ws, rc, cover != 0);
+                long long total = 0;
+                for (const InstDesc& d : g.inst) total += d.units;
+                if (cover) check_slots(total, rc);
+            }
         }
     }
     if (msg && msg_len) {

@@ -28,12 +28,11 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
     }
     __syncwarp();
     const int wpc = blockDim.x >> 5;
-    const long long nwarps = (long long)gridDim.x * wpc;
     int ii = 0;
     unsigned q = 0;
-    // CTA-major slots: the warps of a CTA take neighbouring units (in a batch,
-    // the same kernel specialisation)
-    for (long long uu = (long long)blockIdx.x * wpc + warp; uu < b.total_units; uu += nwarps) {
+    for (long long r = 0;; ++r) {
+        const long long uu = slot_unit(r, blockIdx.x, warp, gridDim.x, wpc, b.total_units);
+        if (uu < 0) break;
         while (ii + 1 < b.n && uu >= b.inst[ii + 1].unit_begin) ++ii;
         const InstDesc& d = b.inst[ii];
         const long long ul = uu - d.unit_begin;

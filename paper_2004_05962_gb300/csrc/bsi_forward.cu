@@ -6,11 +6,11 @@ namespace bsi {
 
 static __device__ unsigned g_err;
 
-// Persistent grid: the warp in slot w = blockIdx.x * warps_per_cta + warp takes
-// units w, w + W, w + 2W, ... of the concatenated unit lists of all instances
-// (W = warps in the grid).  The
-// per-unit work is near-uniform, so the static stride balances without an
-// atomic ticket and is deterministic.
+// Persistent grid: in round r every warp of the launch takes one unit of the
+// concatenated unit lists of all instances (slot_unit, CTA-major: the warps of
+// a CTA take neighbouring units).  The per-unit work is near-uniform,
+// so the static assignment balances without an atomic ticket and is
+// deterministic.
 template <int MAXB, bool BF16, bool GENERIC>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
     bsi_forward_kernel(const __grid_constant__ Batch<MAXB> b) {
@@ -19,12 +19,11 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
     const int warp = threadIdx.x >> 5;
     unsigned char* stage = smem + (size_t)warp * fwd_warp_smem(b.buf_bytes);
     const int wpc = blockDim.x >> 5;
-    const long long nwarps = (long long)gridDim.x * wpc;
     int ii = 0;
     int ring = 0;  // next staging buffer of the warp's store ring
-    // CTA-major slots: the warps of a CTA take neighbouring units, which share
-    // control-point columns in L1 and, in a batch, the same kernel specialisation
-    for (long long uu = (long long)blockIdx.x * wpc + warp; uu < b.total_units; uu += nwarps) {
+    for (long long r = 0;; ++r) {
+        const long long uu = slot_unit(r, blockIdx.x, warp, gridDim.x, wpc, b.total_units, false);
+        if (uu < 0) break;
         while (ii + 1 < b.n && uu >= b.inst[ii + 1].unit_begin) ++ii;
         const InstDesc& d = b.inst[ii];
         const long long ul = uu - d.unit_begin;

@@ -83,6 +83,26 @@ BSI_HD long long phi_elem(const InstDesc& d, int gz, int gy, int gx) {
     return (((long long)gz * d.ny + gy) * d.nx + gx) * 3;
 }
 
+// Unit taken by slot (cta, warp) in round r of a persistent launch of `ctas`
+// CTAs x `wpc` warps over `total` units, or -1 when the slot has none.  Full
+// rounds are CTA-major (the warps of a CTA take neighbouring units, which share
+// control points in L1 and, in a batch, a kernel specialisation); the last,
+// partial round is dealt warp-major across the CTAs (spread_tail) so that every
+// SM gets an even share of it -- worth it for the adjoint's few long units,
+// not for the forward's many short ones.
+BSI_HD long long slot_unit(long long r, int cta, int warp, int ctas, int wpc, long long total,
+                           bool spread_tail = true) {
+    const long long W = (long long)ctas * wpc;
+    const long long base = r * W;
+    if (base >= total) return -1;
+    if (total - base >= W || !spread_tail) {
+        const long long u = base + (long long)cta * wpc + warp;
+        return u < total ? u : -1;
+    }
+    const long long p = (long long)warp * ctas + cta;
+    return p < total - base ? base + p : -1;
+}
+
 // ---------------------------------------------------------------- forward
 
 struct FwdUnit {
