@@ -454,7 +454,9 @@ def run_reference(args, ws, rank):
 
     shape, spacing = CT_SHAPE, CT_SPACING
     Z, Y, X = shape
-    per_step = max(0.5, 150.0 / max(1, args.steps + args.warmup))
+    # each step a z-slab sized so the whole run takes about 150 s of oracle time,
+    # and no step more than --cpu-seconds
+    per_step = min(args.cpu_seconds, max(0.5, 150.0 / max(1, args.steps + args.warmup)))
     phi = synth.gaussian_random_phi(shape, spacing, 3.0, 2.0, seed=2)
     rng = np.random.default_rng(4)
 
