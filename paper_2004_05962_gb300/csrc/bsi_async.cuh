@@ -23,6 +23,27 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// Shared-memory loads and stores by 32-bit shared-window address.  The staging
+// buffers are addressed through these rather than through generic pointers, so
+// every access is a single LDS/STS with an immediate offset and no 64-bit
+// address arithmetic; the predicated forms skip the access without a branch.
+__device__ __forceinline__ float lds_f32_if(uint32_t addr, bool on) {
+    float v = 0.f;
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p ld.shared.f32 %0, [%1];\n\t}"
+                 : "+f"(v) : "r"(addr), "r"((int)on));
+    return v;
+}
+
+__device__ __forceinline__ void sts_f32_if(uint32_t addr, float v, bool on) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p st.shared.f32 [%0], %1;\n\t}"
+                 :: "r"(addr), "f"(v), "r"((int)on) : "memory");
+}
+
+__device__ __forceinline__ void sts_b16_if(uint32_t addr, unsigned short v, bool on) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p st.shared.b16 [%0], %1;\n\t}"
+                 :: "r"(addr), "h"(v), "r"((int)on) : "memory");
+}
+
 // Orders this thread's generic-proxy shared-memory accesses before later
 // async-proxy (bulk copy) accesses of the same memory.
 __device__ __forceinline__ void fence_proxy_async_smem() {

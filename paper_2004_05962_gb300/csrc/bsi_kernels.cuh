@@ -63,18 +63,18 @@ enum : unsigned {
 __device__ __forceinline__ uintptr_t floor16(uintptr_t a) { return a & ~(uintptr_t)15; }
 __device__ __forceinline__ uintptr_t ceil16(uintptr_t a) { return (a + 15) & ~(uintptr_t)15; }
 
+// Stores one voxel's three channels at shared address s (FP32, or BF16 rounded
+// to nearest even), when on.
 template <bool BF16>
-__device__ __forceinline__ void put3(unsigned char* s, int e, float a, float b, float c) {
+__device__ __forceinline__ void put3(uint32_t s, float a, float b, float c, bool on) {
     if (BF16) {
-        __nv_bfloat16* p = reinterpret_cast<__nv_bfloat16*>(s) + e;
-        p[0] = __float2bfloat16_rn(a);
-        p[1] = __float2bfloat16_rn(b);
-        p[2] = __float2bfloat16_rn(c);
+        sts_b16_if(s, __bfloat16_as_ushort(__float2bfloat16_rn(a)), on);
+        sts_b16_if(s + 2, __bfloat16_as_ushort(__float2bfloat16_rn(b)), on);
+        sts_b16_if(s + 4, __bfloat16_as_ushort(__float2bfloat16_rn(c)), on);
     } else {
-        float* p = reinterpret_cast<float*>(s) + e;
-        p[0] = a;
-        p[1] = b;
-        p[2] = c;
+        sts_f32_if(s, a, on);
+        sts_f32_if(s + 4, b, on);
+        sts_f32_if(s + 8, c, on);
     }
 }
 
@@ -112,17 +112,17 @@ __device__ __forceinline__ void store_row(const unsigned char* sb, unsigned char
     }
 }
 
-// x-stage of one voxel of a tile: out = sum_l B_l(r/dx) p_l, per channel.  A
-// voxel outside the strip (on == false) is computed but not stored.
+// x-stage of one voxel of a tile: out = sum_l B_l(r/dx) p_l, per channel,
+// staged at shared address s.  A voxel outside the strip (on == false) is
+// computed but not stored.
 template <bool BF16>
-__device__ __forceinline__ void emit_voxel(unsigned char* sb, int e, int wo, const float (&p0)[3],
-                                           const float (&p1)[3], const float (&p2)[3], const float (&p3)[3],
-                                           bool on) {
+__device__ __forceinline__ void emit_voxel(uint32_t s, int wo, const float (&p0)[3], const float (&p1)[3],
+                                           const float (&p2)[3], const float (&p3)[3], bool on) {
     const float w0 = c_lut.w[wo], w1 = c_lut.w[wo + 1], w2 = c_lut.w[wo + 2], w3 = c_lut.w[wo + 3];
     const float v0 = fmaf(w3, p3[0], fmaf(w2, p2[0], fmaf(w1, p1[0], w0 * p0[0])));
     const float v1 = fmaf(w3, p3[1], fmaf(w2, p2[1], fmaf(w1, p1[1], w0 * p0[1])));
     const float v2 = fmaf(w3, p3[2], fmaf(w2, p2[2], fmaf(w1, p1[2], w0 * p0[2])));
-    if (on) put3<BF16>(sb, e, v0, v1, v2);
+    put3<BF16>(s, v0, v1, v2, on);
 }
 
 // One forward unit: tile-plane kz, tile-row jy, x-group xg.  DX > 0 is a
@@ -197,14 +197,16 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
             ring = ring == kStoreStages - 1 ? 0 : ring + 1;
             // (the ring buffer is free: store_row of the previous row waited for it)
             BSI_GUARD(shift + nbytes <= buf_bytes, kErrStage, err) {
+                // shared address of this lane's first voxel (unused by the halo lanes)
+                const uint32_t sv = smem_u32(sb) + (uint32_t)(3 * ES * xl);
                 if (DX > 0) {  // one predicated path for all lanes: full, cut and halo tiles
 #pragma unroll
                     for (int r = 0; r < (DX > 0 ? DX : 1); ++r)
-                        emit_voxel<BF16>(sb, (xl + r) * 3, weight_base(DX > 0 ? DX : 1) + 4 * r, p0, p1, p2, p3,
+                        emit_voxel<BF16>(sv + 3 * ES * r, weight_base(DX > 0 ? DX : 1) + 4 * r, p0, p1, p2, p3,
                                          r < rn);
                 } else {
                     for (int r = 0; r < rn; ++r)
-                        emit_voxel<BF16>(sb, (xl + r) * 3, wxb + 4 * r, p0, p1, p2, p3, true);
+                        emit_voxel<BF16>(sv + 3 * ES * r, wxb + 4 * r, p0, p1, p2, p3, true);
                 }
             }
             fence_proxy_async_smem();  // this lane's staging writes before the bulk copy reads them
@@ -260,15 +262,11 @@ __device__ __forceinline__ RowLoad row_load(const unsigned char* g, int nbytes, 
     return r;
 }
 
-// x-transpose of one voxel: q_l += B_l(r/dx) g, per channel; a voxel outside
-// the volume (on == false) contributes nothing and is not read.
-__device__ __forceinline__ void gather_voxel(float (&q4)[4][3], const float* sv, int wo, bool on) {
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    if (on) {
-        g0 = sv[0];
-        g1 = sv[1];
-        g2 = sv[2];
-    }
+// x-transpose of one voxel: q_l += B_l(r/dx) g, per channel; the voxel's three
+// channels sit at shared address sv.  A voxel outside the volume (on == false)
+// contributes nothing and is not read.
+__device__ __forceinline__ void gather_voxel(float (&q4)[4][3], uint32_t sv, int wo, bool on) {
+    const float g0 = lds_f32_if(sv, on), g1 = lds_f32_if(sv + 4, on), g2 = lds_f32_if(sv + 8, on);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
         const float w = c_lut.w[wo + l];
@@ -376,7 +374,8 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
                     }
                 }
                 __syncwarp();
-                const float* sv = reinterpret_cast<const float*>(sb) + xl * 3;
+                // shared address of this lane's first voxel (unused when the lane has none)
+                const uint32_t sv = smem_u32(sb) + 12u * (uint32_t)xl;
                 float q4[4][3];
 #pragma unroll
                 for (int l = 0; l < 4; ++l)
@@ -385,14 +384,19 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
                 if (DX > 0) {  // one predicated path for all lanes: full, cut and empty tiles
 #pragma unroll
                     for (int r = 0; r < (DX > 0 ? DX : 1); ++r)
-                        gather_voxel(q4, sv + 3 * r, weight_base(DX > 0 ? DX : 1) + 4 * r, r < nv);
+                        gather_voxel(q4, sv + 12u * r, weight_base(DX > 0 ? DX : 1) + 4 * r, r < nv);
                 } else {
-                    for (int r = 0; r < nv; ++r) gather_voxel(q4, sv + 3 * r, wxb + 4 * r, true);
+                    for (int r = 0; r < nv; ++r) gather_voxel(q4, sv + 12u * r, wxb + 4 * r, true);
                 }
                 // this ring buffer may be refilled once every lane has read it
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0 && ik < rows) issue_next();
+                // refill in pairs: after every second row the two freed ring buffers
+                // get the next two rows, one lane-0 block for both copies
+                if (lane == 0 && (k & 1) && ik < rows) {
+                    issue_next();
+                    if (ik < rows) issue_next();
+                }
 
                 // column sum: the column of lane l collects q4[k] of the tile k lanes below
                 const float b0 = c_lut.w[wyb + 4 * ry], b1 = c_lut.w[wyb + 4 * ry + 1];
