@@ -170,11 +170,12 @@ bsi_status bsi_field_adjoint_noalloc(const bsi_geom* g, const float* grad_field,
 typedef struct {
     int32_t dx, dy, dz;        /* spacing the entry applies to; 0 matches any value */
     int32_t adj_zchunk;        /* adjoint: tile-planes per warp unit, 3..16 (default 4) */
-    int32_t adj_warps;         /* adjoint: warps per CTA, 1..8 (default 8, fewer if shared
+    int32_t adj_warps;         /* adjoint: warps per CTA, 1..4 (default 4, fewer if shared
                                   memory requires) */
     int32_t fwd_strip_tiles;   /* forward: tiles per warp strip, 4..29 (default 28 or 29,
                                   whichever keeps FP32 rows 16-byte aligned) */
-    int32_t fwd_warps;         /* forward: warps per CTA, 1..8 (default as adj_warps) */
+    int32_t fwd_warps;         /* forward: warps per CTA, 1..8 (default 8, fewer if shared
+                                  memory requires) */
 } bsi_tile_config;
 
 #define BSI_MAX_TILE_CONFIGS 256

@@ -102,7 +102,7 @@ static bool config_valid(const bsi_tile_config& c) {
     auto sp = [](int32_t v) { return v == 0 || (v >= 1 && v <= BSI_MAX_SPACING); };
     return sp(c.dx) && sp(c.dy) && sp(c.dz) && (c.adj_zchunk == 0 || (c.adj_zchunk >= 3 && c.adj_zchunk <= 16)) &&
            (c.fwd_strip_tiles == 0 || (c.fwd_strip_tiles >= 4 && c.fwd_strip_tiles <= kGroupCells)) &&
-           (c.adj_warps >= 0 && c.adj_warps <= kMaxWarpsPerCta) &&
+           (c.adj_warps >= 0 && c.adj_warps <= kAdjWarpsMax) &&
            (c.fwd_warps >= 0 && c.fwd_warps <= kMaxWarpsPerCta);
 }
 
@@ -565,7 +565,7 @@ bsi_status bsi_get_tile_config(int32_t dx, int32_t dy, int32_t dz, bsi_tile_conf
     c.dy = dy;
     c.dz = dz;
     if (c.adj_zchunk == 0) c.adj_zchunk = kDefaultZChunk;
-    if (c.adj_warps == 0) c.adj_warps = kMaxWarpsPerCta;
+    if (c.adj_warps == 0) c.adj_warps = kAdjWarpsMax;
     if (c.fwd_warps == 0) c.fwd_warps = kMaxWarpsPerCta;
     // fwd_strip_tiles stays 0 when unset: it then depends on the volume (X % 4) and dtype
     *out = c;

@@ -12,8 +12,13 @@ namespace bsi {
 
 static __device__ unsigned g_err;
 
+// 4-warp CTAs, 3 per SM: the unit's rolling z window (48 accumulators per lane)
+// fits in <= 170 registers without spilling; measured ~4% faster than 8-warp
+// CTAs capped at 128 registers.
+constexpr int kAdjMaxWarps = kAdjWarpsMax;
+
 template <int MAXB, bool GENERIC>
-__global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
+__global__ void __launch_bounds__(kAdjMaxWarps * kLanes, 3)
     bsi_adjoint_partials_kernel(const __grid_constant__ Batch<MAXB> b, float* __restrict__ part,
                                 long long ws_floats) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -130,7 +135,8 @@ template <int MAXB, bool GENERIC>
 static cudaError_t launch_part_t(const Batch<MAXB>& b, float* part, long long ws_floats, cudaStream_t s,
                                  LaunchInfo* info) {
     auto kern = bsi_adjoint_partials_kernel<MAXB, GENERIC>;
-    const int wpc = warps_per_cta(adj_warp_smem(b.buf_bytes), b.warps_req);
+    const int wpc = warps_per_cta(adj_warp_smem(b.buf_bytes),
+                                  b.warps_req > 0 && b.warps_req < kAdjMaxWarps ? b.warps_req : kAdjMaxWarps);
     const int threads = wpc * kLanes;
     const int smem = wpc * adj_warp_smem(b.buf_bytes);
     KernelFacts f;

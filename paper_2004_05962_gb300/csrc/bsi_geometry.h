@@ -189,6 +189,7 @@ BSI_HD int fwd_warp_smem(int buf_bytes) { return kStoreStages * buf_bytes; }
 BSI_HD int adj_warp_smem(int buf_bytes) { return kLoadStages * (16 + buf_bytes); }
 
 constexpr int kMaxWarpsPerCta = 8;
+constexpr int kAdjWarpsMax = 4;   // adjoint partials kernel: 4-warp CTAs (register budget)
 constexpr int kSmemBudget = 200 * 1024;   // dynamic shared memory per CTA we allow
 
 // Warps per CTA such that the warps' shared memory fits the budget, at most

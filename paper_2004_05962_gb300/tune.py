@@ -28,7 +28,8 @@ DEFAULT_CACHE = pathlib.Path(__file__).resolve().parent / "_build" / "tile_confi
 
 FWD_STRIPS = (0, 24, 20, 16)          # 0: the library's aligned default (28 or 29)
 ADJ_ZCHUNKS = (3, 4, 5, 6, 8)
-WARPS = (0, 4)                        # 0: as many as shared memory allows (8)
+WARPS = (0, 4)                        # forward, 0: as many as shared memory allows (8)
+ADJ_WARPS = (0, 2)                    # adjoint, 0: the default 4
 
 
 def _key(spacing, dtype, dev):
@@ -87,7 +88,7 @@ def tune_spacing(spacing, shape=None, dtype=torch.float32, iters=10, device=None
                     best_f, best_f_ms = cfg, ms
         best_a, best_a_ms = None, float("inf")
         for zc in ADJ_ZCHUNKS:
-            for w in WARPS:
+            for w in ADJ_WARPS:
                 cfg = dict(base, adj_zchunk=zc, adj_warps=w)
                 B.bsi_set_tile_configs([cfg])
                 ws = torch.empty(B.bsi_adjoint_workspace_bytes(shape, spacing), dtype=torch.uint8, device=dev)
@@ -155,7 +156,7 @@ def tune_batched(shapes, spacings, dtype=torch.float32, cache_path=DEFAULT_CACHE
                         best_f, best_f_ms = cfg, ms
             best_a, best_a_ms = None, float("inf")
             for zc in ADJ_ZCHUNKS:
-                for w in WARPS:
+                for w in ADJ_WARPS:
                     cfg = {"adj_zchunk": zc, "adj_warps": w}
                     B.bsi_set_tile_configs([cfg])
                     ws = torch.empty(B.bsi_batched_adjoint_workspace_bytes(shapes, spacings), dtype=torch.uint8,

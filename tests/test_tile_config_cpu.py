@@ -19,18 +19,18 @@ def clean_table():
 
 def test_defaults_and_lookup():
     d = B.bsi_get_tile_config((5, 5, 5))
-    assert d == {"dx": 5, "dy": 5, "dz": 5, "adj_zchunk": 4, "adj_warps": 8, "fwd_strip_tiles": 0, "fwd_warps": 8}
+    assert d == {"dx": 5, "dy": 5, "dz": 5, "adj_zchunk": 4, "adj_warps": 4, "fwd_strip_tiles": 0, "fwd_warps": 8}
     B.bsi_set_tile_configs([{"dx": 5, "dy": 5, "dz": 5, "adj_zchunk": 6},
                             {"dx": 3, "adj_zchunk": 8, "fwd_strip_tiles": 16},
-                            {"adj_warps": 4}])
+                            {"adj_warps": 2}])
     assert B.bsi_get_tile_config((5, 5, 5))["adj_zchunk"] == 6
     assert B.bsi_get_tile_config((7, 9, 3))["fwd_strip_tiles"] == 16      # dx wildcard entry
-    assert B.bsi_get_tile_config((7, 9, 4))["adj_warps"] == 4            # catch-all entry
+    assert B.bsi_get_tile_config((7, 9, 4))["adj_warps"] == 2            # catch-all entry
     assert B.bsi_tile_configs()[1]["dx"] == 3
 
 
 @pytest.mark.parametrize("bad", [{"adj_zchunk": 2}, {"adj_zchunk": 17}, {"fwd_strip_tiles": 3},
-                                 {"fwd_strip_tiles": 30}, {"adj_warps": 9}, {"fwd_warps": -1}, {"dx": 65}])
+                                 {"fwd_strip_tiles": 30}, {"adj_warps": 5}, {"fwd_warps": -1}, {"dx": 65}])
 def test_invalid_entries_rejected_and_table_kept(bad):
     B.bsi_set_tile_configs([{"adj_zchunk": 5}])
     with pytest.raises(B.BsiError):
