@@ -369,7 +369,9 @@ static void check_forward_group(const Group& g, int es, RangeChecker& rc, bool c
             }
             const int z0 = u.kz * d.dz, zn = imin(d.dz, d.Z - z0);
             const int y0 = u.jy * d.dy, yn = imin(d.dy, d.Y - y0);
-            if (15 + u.nvox * 3 * es > buf) rc.fail("staging overflow", u.nvox, buf);
+            // a specialised spacing stages all 32 lanes x dx voxels (past the row end too)
+            const int staged = d.dx <= kMaxSpecializedDx && !g.generic ? kLanes * d.dx : u.nvox;
+            if (u.nvox > staged || 15 + staged * 3 * es > buf) rc.fail("staging overflow", staged, buf);
             if (warps_per_cta(fwd_warp_smem(buf)) * fwd_warp_smem(buf) > kSmemBudget)
                 rc.fail("forward shared memory over budget", buf, kSmemBudget);
             for (int rz = 0; rz < zn; ++rz)
@@ -399,6 +401,17 @@ static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecke
             if (u.kz1 <= u.kz0) rc.fail("adjoint unit without planes", ul, u.kz0);
             // a bulk load covers the 16-byte-aligned superset of the row: <= nbytes + 30
             if (30 + u.nvox * 12 > buf) rc.fail("staging overflow", u.nvox, buf);
+            // unpredicated reads of a specialised spacing: every lane reads dx voxels,
+            // inside [0, nvox) or, in a ragged unit, the zeros [nvox, nvox + zv)
+            const bool spec = d.dx <= kMaxSpecializedDx && !g.generic;
+            bool ragged = false;
+            for (int lane = 0; lane < kLanes; ++lane) {
+                const int cell = u.col0 - kHalo + lane;
+                const int nv = (cell >= 0 && cell < d.ncx) ? imin(d.dx, d.X - cell * d.dx) : 0;
+                ragged = ragged || nv != d.dx;
+            }
+            const int zv = imin(d.dx, kLanes * d.dx - u.nvox);
+            if (spec && ragged && 15 + 12 * (u.nvox + zv) > buf) rc.fail("zeroed tail overflow", u.nvox + zv, buf);
             if (warps_per_cta(adj_warp_smem(buf)) * adj_warp_smem(buf) > kSmemBudget)
                 rc.fail("adjoint shared memory over budget", buf, kSmemBudget);
             for (int lane = 0; lane < kLanes; ++lane) {
@@ -406,6 +419,13 @@ static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecke
                 const int nv = (cell >= 0 && cell < d.ncx) ? imin(d.dx, d.X - cell * d.dx) : 0;
                 const int xl = cell * d.dx - u.xs;
                 if (nv > 0 && (xl < 0 || xl + nv > u.nvox)) rc.fail("lane voxels outside strip", xl, u.nvox);
+                if (spec) {
+                    const int rl = nv == 0 ? u.nvox : xl;   // the kernel's read start
+                    if (rl < 0 || rl + d.dx > (ragged ? u.nvox + zv : u.nvox))
+                        rc.fail("unpredicated read outside row and zeros", rl, u.nvox);
+                    if (nv > 0 && nv < d.dx && xl + nv != u.nvox)   // its missing voxels are the zeros
+                        rc.fail("cut tile does not end at the row end", xl + nv, u.nvox);
+                }
                 const int j = lane - kHalo;
                 if (j < 0 || u.col0 + j >= d.nx) continue;
                 for (int pz = 0; pz < u.kz1 - u.kz0 + kHalo; ++pz)

@@ -26,22 +26,40 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 // Shared-memory loads and stores by 32-bit shared-window address.  The staging
 // buffers are addressed through these rather than through generic pointers, so
 // every access is a single LDS/STS with an immediate offset and no 64-bit
-// address arithmetic; the predicated forms skip the access without a branch.
-__device__ __forceinline__ float lds_f32_if(uint32_t addr, bool on) {
-    float v = 0.f;
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p ld.shared.f32 %0, [%1];\n\t}"
-                 : "+f"(v) : "r"(addr), "r"((int)on));
+// address arithmetic.  They are unpredicated: the kernels lay out their
+// staging rows so that every lane's accesses stay inside its warp's buffer
+// (reads of voxels outside the volume hit zeroed bytes, writes past the row
+// end are never copied out).
+__device__ __forceinline__ float lds_f32(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
     return v;
 }
 
-__device__ __forceinline__ void sts_f32_if(uint32_t addr, float v, bool on) {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p st.shared.f32 [%0], %1;\n\t}"
-                 :: "r"(addr), "f"(v), "r"((int)on) : "memory");
+__device__ __forceinline__ void sts_f32(uint32_t addr, float v) {
+    asm volatile("st.shared.f32 [%0], %1;" :: "r"(addr), "f"(v) : "memory");
 }
 
-__device__ __forceinline__ void sts_b16_if(uint32_t addr, unsigned short v, bool on) {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %2, 0;\n\t@p st.shared.b16 [%0], %1;\n\t}"
-                 :: "r"(addr), "h"(v), "r"((int)on) : "memory");
+// Vector forms: addr must be 8-byte (v2) or 16-byte (v4) aligned.
+__device__ __forceinline__ void lds_v2_f32(uint32_t addr, float& a, float& b) {
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "r"(addr));
+}
+
+__device__ __forceinline__ void lds_v4_f32(uint32_t addr, float& a, float& b, float& c, float& d) {
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(a), "=f"(b), "=f"(c), "=f"(d) : "r"(addr));
+}
+
+__device__ __forceinline__ void sts_v2_f32(uint32_t addr, float a, float b) {
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" :: "r"(addr), "f"(a), "f"(b) : "memory");
+}
+
+__device__ __forceinline__ void sts_v4_f32(uint32_t addr, float a, float b, float c, float d) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" :: "r"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ void sts_b16(uint32_t addr, unsigned short v) {
+    asm volatile("st.shared.b16 [%0], %1;" :: "r"(addr), "h"(v) : "memory");
 }
 
 // Orders this thread's generic-proxy shared-memory accesses before later

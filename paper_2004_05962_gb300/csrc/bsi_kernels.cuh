@@ -64,17 +64,17 @@ __device__ __forceinline__ uintptr_t floor16(uintptr_t a) { return a & ~(uintptr
 __device__ __forceinline__ uintptr_t ceil16(uintptr_t a) { return (a + 15) & ~(uintptr_t)15; }
 
 // Stores one voxel's three channels at shared address s (FP32, or BF16 rounded
-// to nearest even), when on.
+// to nearest even).
 template <bool BF16>
-__device__ __forceinline__ void put3(uint32_t s, float a, float b, float c, bool on) {
+__device__ __forceinline__ void put3(uint32_t s, float a, float b, float c) {
     if (BF16) {
-        sts_b16_if(s, __bfloat16_as_ushort(__float2bfloat16_rn(a)), on);
-        sts_b16_if(s + 2, __bfloat16_as_ushort(__float2bfloat16_rn(b)), on);
-        sts_b16_if(s + 4, __bfloat16_as_ushort(__float2bfloat16_rn(c)), on);
+        sts_b16(s, __bfloat16_as_ushort(__float2bfloat16_rn(a)));
+        sts_b16(s + 2, __bfloat16_as_ushort(__float2bfloat16_rn(b)));
+        sts_b16(s + 4, __bfloat16_as_ushort(__float2bfloat16_rn(c)));
     } else {
-        sts_f32_if(s, a, on);
-        sts_f32_if(s + 4, b, on);
-        sts_f32_if(s + 8, c, on);
+        sts_f32(s, a);
+        sts_f32(s + 4, b);
+        sts_f32(s + 8, c);
     }
 }
 
@@ -113,16 +113,52 @@ __device__ __forceinline__ void store_row(const unsigned char* sb, unsigned char
 }
 
 // x-stage of one voxel of a tile: out = sum_l B_l(r/dx) p_l, per channel,
-// staged at shared address s.  A voxel outside the strip (on == false) is
-// computed but not stored.
+// staged at shared address s.
 template <bool BF16>
 __device__ __forceinline__ void emit_voxel(uint32_t s, int wo, const float (&p0)[3], const float (&p1)[3],
-                                           const float (&p2)[3], const float (&p3)[3], bool on) {
+                                           const float (&p2)[3], const float (&p3)[3]) {
     const float w0 = c_lut.w[wo], w1 = c_lut.w[wo + 1], w2 = c_lut.w[wo + 2], w3 = c_lut.w[wo + 3];
     const float v0 = fmaf(w3, p3[0], fmaf(w2, p2[0], fmaf(w1, p1[0], w0 * p0[0])));
     const float v1 = fmaf(w3, p3[1], fmaf(w2, p2[1], fmaf(w1, p1[1], w0 * p0[1])));
     const float v2 = fmaf(w3, p3[2], fmaf(w2, p2[2], fmaf(w1, p1[2], w0 * p0[2])));
-    put3<BF16>(s, v0, v1, v2, on);
+    put3<BF16>(s, v0, v1, v2);
+}
+
+// Shared-memory vector width (floats) for staging the 3 DX FP32 values of one
+// lane's tile: a lane's tile starts 12 DX bytes after its neighbour's, so with
+// DX a multiple of 4 (2) and an aligned row start it can move 16 (8) bytes per
+// access -- 4 (2) times fewer LDS/STS, and for DX = 4, 6, 8 fewer bank
+// conflicts than the 12 DX-byte scalar stride.
+template <int DX>
+__host__ __device__ constexpr int tile_vec() {
+    return DX <= 0 ? 1 : (DX % 4 == 0 ? 4 : (DX % 2 == 0 ? 2 : 1));
+}
+
+// x-stage of a whole tile of DX voxels staged from shared address sv, with
+// VW-float stores (VW > 1: FP32 only, sv aligned to 4 VW bytes).
+template <int DX, int VW, bool BF16>
+__device__ __forceinline__ void emit_tile(uint32_t sv, const float (&p0)[3], const float (&p1)[3],
+                                          const float (&p2)[3], const float (&p3)[3]) {
+    constexpr int ES = BF16 ? 2 : 4;
+    if (VW == 1) {
+#pragma unroll
+        for (int r = 0; r < DX; ++r) emit_voxel<BF16>(sv + 3 * ES * r, weight_base(DX) + 4 * r, p0, p1, p2, p3);
+    } else {
+        float v[3 * DX];
+#pragma unroll
+        for (int r = 0; r < DX; ++r) {
+            const int wo = weight_base(DX) + 4 * r;
+            const float w0 = c_lut.w[wo], w1 = c_lut.w[wo + 1], w2 = c_lut.w[wo + 2], w3 = c_lut.w[wo + 3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                v[3 * r + c] = fmaf(w3, p3[c], fmaf(w2, p2[c], fmaf(w1, p1[c], w0 * p0[c])));
+        }
+#pragma unroll
+        for (int i = 0; i < 3 * DX / VW; ++i) {
+            if (VW == 4) sts_v4_f32(sv + 16 * i, v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            else sts_v2_f32(sv + 8 * i, v[2 * i], v[2 * i + 1]);
+        }
+    }
 }
 
 // One forward unit: tile-plane kz, tile-row jy, x-group xg.  DX > 0 is a
@@ -196,17 +232,19 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
             unsigned char* sb = stage + ring * buf_bytes + shift;
             ring = ring == kStoreStages - 1 ? 0 : ring + 1;
             // (the ring buffer is free: store_row of the previous row waited for it)
-            BSI_GUARD(shift + nbytes <= buf_bytes, kErrStage, err) {
-                // shared address of this lane's first voxel (unused by the halo lanes)
+            BSI_GUARD(shift + (DX > 0 ? 3 * ES * kLanes * DX : nbytes) <= buf_bytes, kErrStage, err) {
+                // shared address of this lane's first voxel
                 const uint32_t sv = smem_u32(sb) + (uint32_t)(3 * ES * xl);
-                if (DX > 0) {  // one predicated path for all lanes: full, cut and halo tiles
-#pragma unroll
-                    for (int r = 0; r < (DX > 0 ? DX : 1); ++r)
-                        emit_voxel<BF16>(sv + 3 * ES * r, weight_base(DX > 0 ? DX : 1) + 4 * r, p0, p1, p2, p3,
-                                         r < rn);
+                if (DX > 0) {
+                    // every lane stages all DX voxels of its tile, unpredicated: a cut or
+                    // halo tile lands past the row end, inside the buffer (lane 31 ends at
+                    // 32 DX voxels), and only [shift, shift + nbytes) is copied out
+                    constexpr int DXS = DX > 0 ? DX : 1;
+                    constexpr int VW = BF16 ? 1 : tile_vec<DXS>();
+                    if (VW > 1 && (shift & (4 * VW - 1)) == 0) emit_tile<DXS, VW, BF16>(sv, p0, p1, p2, p3);
+                    else emit_tile<DXS, 1, BF16>(sv, p0, p1, p2, p3);
                 } else {
-                    for (int r = 0; r < rn; ++r)
-                        emit_voxel<BF16>(sv + 3 * ES * r, wxb + 4 * r, p0, p1, p2, p3, true);
+                    for (int r = 0; r < rn; ++r) emit_voxel<BF16>(sv + 3 * ES * r, wxb + 4 * r, p0, p1, p2, p3);
                 }
             }
             fence_proxy_async_smem();  // this lane's staging writes before the bulk copy reads them
@@ -263,16 +301,40 @@ __device__ __forceinline__ RowLoad row_load(const unsigned char* g, int nbytes, 
 }
 
 // x-transpose of one voxel: q_l += B_l(r/dx) g, per channel; the voxel's three
-// channels sit at shared address sv.  A voxel outside the volume (on == false)
-// contributes nothing and is not read.
-__device__ __forceinline__ void gather_voxel(float (&q4)[4][3], uint32_t sv, int wo, bool on) {
-    const float g0 = lds_f32_if(sv, on), g1 = lds_f32_if(sv + 4, on), g2 = lds_f32_if(sv + 8, on);
+// channels sit at shared address sv.
+__device__ __forceinline__ void gather_voxel(float (&q4)[4][3], uint32_t sv, int wo) {
+    const float g0 = lds_f32(sv), g1 = lds_f32(sv + 4), g2 = lds_f32(sv + 8);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
         const float w = c_lut.w[wo + l];
         q4[l][0] = fmaf(w, g0, q4[l][0]);
         q4[l][1] = fmaf(w, g1, q4[l][1]);
         q4[l][2] = fmaf(w, g2, q4[l][2]);
+    }
+}
+
+// x-transpose of a whole tile of DX voxels read from shared address sv with
+// VW-float loads (sv aligned to 4 VW bytes; see tile_vec).
+template <int DX, int VW>
+__device__ __forceinline__ void gather_tile(float (&q4)[4][3], uint32_t sv) {
+    if (VW == 1) {
+#pragma unroll
+        for (int r = 0; r < DX; ++r) gather_voxel(q4, sv + 12u * r, weight_base(DX) + 4 * r);
+    } else {
+        float g[3 * DX];
+#pragma unroll
+        for (int i = 0; i < 3 * DX / VW; ++i) {
+            if (VW == 4) lds_v4_f32(sv + 16 * i, g[4 * i], g[4 * i + 1], g[4 * i + 2], g[4 * i + 3]);
+            else lds_v2_f32(sv + 8 * i, g[2 * i], g[2 * i + 1]);
+        }
+#pragma unroll
+        for (int r = 0; r < DX; ++r)
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const float w = c_lut.w[weight_base(DX) + 4 * r + l];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) q4[l][c] = fmaf(w, g[3 * r + c], q4[l][c]);
+            }
     }
 }
 
@@ -284,7 +346,16 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
     const AdjUnit u = adj_unit(d, ul);
     const int cell = u.col0 - kHalo + lane;
     const int nv = (cell >= 0 && cell < d.ncx) ? imin(dx, d.X - cell * dx) : 0;
-    const int xl = cell * dx - u.xs;      // strip-local first voxel of this lane's tile
+    // A specialised spacing reads all DX voxels of every lane, unpredicated.  In
+    // a ragged unit (a cut or empty tile: the first and last x-groups) each
+    // staged row gets zfloats zeros right after its nvox voxels; a cut tile
+    // reads its missing voxels there and an empty tile reads all of its voxels
+    // there, so both add exact zeros.  The zeros end by voxel 32 DX of the
+    // strip, inside the ring buffer.
+    const bool ragged = DX > 0 && !__all_sync(kFull, nv == dx);
+    const int zfloats = 3 * imin(dx, kLanes * dx - u.nvox);
+    // strip-local first voxel of this lane's tile (empty tiles: the zeros)
+    const int xl = (DX > 0 && nv == 0) ? u.nvox : cell * dx - u.xs;
     const int y0 = u.jy * d.dy, yn = imin(d.dy, d.Y - y0);
     const int zb = u.kz0 * d.dz;
     const int rows = (imin(u.kz1 * d.dz, d.Z) - zb) * yn;
@@ -373,20 +444,31 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
                         }
                     }
                 }
+                BSI_GUARD((int)(g & 15) + 12 * u.nvox + 4 * zfloats <= buf_bytes, kErrStage, err) {
+                    if (ragged && lane < zfloats) sts_f32(smem_u32(sb) + 12u * (uint32_t)u.nvox + 4u * lane, 0.f);
+                }
                 __syncwarp();
-                // shared address of this lane's first voxel (unused when the lane has none)
+                // shared address of this lane's first voxel
                 const uint32_t sv = smem_u32(sb) + 12u * (uint32_t)xl;
                 float q4[4][3];
 #pragma unroll
                 for (int l = 0; l < 4; ++l)
 #pragma unroll
                     for (int c = 0; c < 3; ++c) q4[l][c] = 0.f;
-                if (DX > 0) {  // one predicated path for all lanes: full, cut and empty tiles
-#pragma unroll
-                    for (int r = 0; r < (DX > 0 ? DX : 1); ++r)
-                        gather_voxel(q4, sv + 12u * r, weight_base(DX > 0 ? DX : 1) + 4 * r, r < nv);
+                if (DX > 0) {  // one path for all lanes: full, cut and empty tiles
+                    constexpr int DXS = DX > 0 ? DX : 1;
+                    // 16-byte loads for DX = 4, 8 (8-byte loads for DX = 2, 6 measured slower
+                    // than scalar ones)
+                    constexpr int VW = DXS % 4 == 0 ? 4 : 1;
+                    // vector loads when every lane's start is aligned (warp-uniform): the
+                    // row start, and in a ragged unit the zeros after nvox voxels
+                    const uint32_t amask = 4 * VW - 1;
+                    if (VW > 1 && ((uint32_t)g & amask) == 0 && (!ragged || ((12u * u.nvox) & amask) == 0))
+                        gather_tile<DXS, VW>(q4, sv);
+                    else
+                        gather_tile<DXS, 1>(q4, sv);
                 } else {
-                    for (int r = 0; r < nv; ++r) gather_voxel(q4, sv + 12u * r, wxb + 4 * r, true);
+                    for (int r = 0; r < nv; ++r) gather_voxel(q4, sv + 12u * r, wxb + 4 * r);
                 }
                 // this ring buffer may be refilled once every lane has read it
                 fence_proxy_async_smem();
