@@ -1,5 +1,6 @@
 // bsi_abi.cu -- the C ABI declared in include/bsi.h: host-side validation,
 // launch planning and the host-only range self-check.
+#include <cudaTypedefs.h>   // PFN_cuTensorMapEncodeTiled
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -157,33 +158,50 @@ static long long adj_floats(const InstDesc& d) {
 // A launch group: up to kMaxBatch instances that share a kernel variant.
 struct Group {
     bool generic = false;
+    bool tma = false;    // adjoint tensor-copy path
     int dxmax = 1;
+    int dymax = 1;
     int warps_req = 0;   // smallest non-zero warps_per_cta request of its instances
     std::vector<InstDesc> inst;
 };
 
-// Splits instances into groups of one kernel variant (x-spacing <= 8 takes the
-// compile-time-specialised kernel, larger spacings the generic one), in caller
-// order, at most kMaxBatch per group; fills unit/point prefixes and partial offsets.
-static std::vector<Group> plan(const std::vector<InstDesc>& all, long long* ws_floats) {
+static bool misaligned(const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) != 0; }
+
+// Whether an adjoint instance can take the tensor-copy path: rows of 16-byte
+// multiples in a 16-byte-aligned array, a box of <= 8 rows and x-spacing <= 8.
+static bool tma_geometry_ok(const InstDesc& d) {
+    return d.units > 0 && d.dx <= kMaxSpecializedDx && d.dy <= kTmaMaxDy && d.X % 4 == 0 && !misaligned(d.grad, 16);
+}
+
+// Splits instances into groups of one kernel variant, in caller order, at most
+// kMaxBatch per group: with allow_tma, adjoint instances that can take the
+// tensor-copy path (tma_geometry_ok); then x-spacing <= 8 (the
+// compile-time-specialised kernel); then larger spacings (the generic one).
+// Fills unit/point prefixes and partial offsets.
+static std::vector<Group> plan(const std::vector<InstDesc>& all, long long* ws_floats, bool allow_tma = false) {
     std::vector<Group> out;
     long long off = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool generic = pass == 1;
+    for (int pass = 0; pass < 3; ++pass) {
+        const bool tma = pass == 0, generic = pass == 2;
+        if (tma && !allow_tma) continue;
         Group cur;
         cur.generic = generic;
+        cur.tma = tma;
         for (const InstDesc& d0 : all) {
-            if ((d0.dx > kMaxSpecializedDx) != generic) continue;
+            const bool t = allow_tma && tma_geometry_ok(d0);
+            if (t != tma || (!t && (d0.dx > kMaxSpecializedDx) != generic)) continue;
             InstDesc d = d0;
             d.part_off = off;
             off += adj_floats(d);
             cur.inst.push_back(d);
             cur.dxmax = std::max(cur.dxmax, d.dx);
+            cur.dymax = std::max(cur.dymax, d.dy);
             if (d.warps_req > 0 && (cur.warps_req == 0 || d.warps_req < cur.warps_req)) cur.warps_req = d.warps_req;
             if ((int)cur.inst.size() == kMaxBatch) {
                 out.push_back(cur);
                 cur.inst.clear();
                 cur.dxmax = 1;
+                cur.dymax = 1;
                 cur.warps_req = 0;
             }
         }
@@ -206,8 +224,9 @@ template <int MAXB>
 static void to_batch(const Group& g, Batch<MAXB>& b) {
     std::memset(&b, 0, sizeof b);
     b.n = (int)g.inst.size();
-    b.buf_bytes = stage_buf_bytes(g.dxmax);
-    b.warps_req = g.warps_req;
+    b.buf_bytes = g.tma ? tma_stage_bytes(g.dxmax, g.dymax) : stage_buf_bytes(g.dxmax);
+    b.stages = g.tma ? kTmaDefaultStages : 0;
+    b.warps_req = g.tma ? 0 : g.warps_req;
     for (int i = 0; i < b.n; ++i) {
         b.inst[i] = g.inst[i];
         b.total_units += g.inst[i].units;
@@ -215,7 +234,49 @@ static void to_batch(const Group& g, Batch<MAXB>& b) {
     }
 }
 
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link against
+// the driver library); null when the driver does not provide it.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult qr = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) !=
+                cudaSuccess ||
+            qr != cudaDriverEntryPointSuccess) {
+            (void)cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// The gradient of one instance as a 3-D tensor of 8-byte elements (float
+// pairs): (3X/2, Y, Z), with a box of (tma_box_width(dx), dy, 1); zeros outside.
+static cudaError_t encode_grad_map(const InstDesc& d, CUtensorMap* m) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[3] = {(cuuint64_t)d.X * 3 / 2, (cuuint64_t)d.Y, (cuuint64_t)d.Z};
+    const cuuint64_t strides[2] = {(cuuint64_t)d.X * 12, (cuuint64_t)d.X * 12 * (cuuint64_t)d.Y};
+    const cuuint32_t box[3] = {(cuuint32_t)tma_box_width(d.dx), (cuuint32_t)d.dy, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float*>(d.grad), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 enum class Op { Forward, AdjointPartials, AdjointReduce };
+
+template <int MAXB>
+static cudaError_t run_partials_tma(const Group& g, const Batch<MAXB>& b, TmaMaps<MAXB>& maps, float* part,
+                                    long long ws_floats, cudaStream_t s) {
+    for (int i = 0; i < b.n; ++i) {
+        const cudaError_t e = encode_grad_map(g.inst[(size_t)i], &maps.m[i]);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_adjoint_partials_tma(b, maps, part, ws_floats, s, nullptr);
+}
 
 static cudaError_t run_group(const Group& g, Op op, bool bf16, float* part, long long ws_floats,
                              cudaStream_t s) {
@@ -224,17 +285,27 @@ static cudaError_t run_group(const Group& g, Op op, bool bf16, float* part, long
         Batch<1> b;
         to_batch(g, b);
         if (op == Op::Forward) return launch_forward(b, bf16, g.generic, s, nullptr);
-        if (op == Op::AdjointPartials) return launch_adjoint_partials(b, g.generic, part, ws_floats, s, nullptr);
+        if (op == Op::AdjointPartials) {
+            if (g.tma) {
+                TmaMaps<1> maps;
+                return run_partials_tma(g, b, maps, part, ws_floats, s);
+            }
+            return launch_adjoint_partials(b, g.generic, part, ws_floats, s, nullptr);
+        }
         return launch_adjoint_reduce(b, part, ws_floats, s, nullptr);
     }
     static thread_local Batch<kMaxBatch> b;  // ~9 KB: kept off the stack
     to_batch(g, b);
     if (op == Op::Forward) return launch_forward(b, bf16, g.generic, s, nullptr);
-    if (op == Op::AdjointPartials) return launch_adjoint_partials(b, g.generic, part, ws_floats, s, nullptr);
+    if (op == Op::AdjointPartials) {
+        if (g.tma) {
+            static thread_local TmaMaps<kMaxBatch> maps;  // 8 KB
+            return run_partials_tma(g, b, maps, part, ws_floats, s);
+        }
+        return launch_adjoint_partials(b, g.generic, part, ws_floats, s, nullptr);
+    }
     return launch_adjoint_reduce(b, part, ws_floats, s, nullptr);
 }
-
-static bool misaligned(const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) != 0; }
 
 static bsi_status check_instances(const bsi_instance* inst, int n, bool fwd, bool adj, bsi_dtype dt) {
     if (n < 0 || (n > 0 && !inst)) return BSI_ERR_BATCH;
@@ -284,7 +355,7 @@ static bsi_status adjoint_impl(const bsi_instance* inst, int n, void* ws, size_t
     bsi_status st = check_instances(inst, n, false, true, BSI_F32);
     if (st != BSI_OK) return st;
     long long ws_floats = 0;
-    const std::vector<Group> groups = plan(descs(inst, n, true), &ws_floats);
+    const std::vector<Group> groups = plan(descs(inst, n, true), &ws_floats, tensor_map_encoder() != nullptr);
     if ((size_t)ws_floats * sizeof(float) > ws_bytes) return BSI_ERR_WORKSPACE;
     if (ws_floats > 0 && !ws) return BSI_ERR_WORKSPACE;
     if (ws && misaligned(ws, 16)) return BSI_ERR_ALIGN;
@@ -399,11 +470,34 @@ static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecke
         for (long long ul = 0; ul < d.units; ++ul) {
             const AdjUnit u = adj_unit(d, ul);
             if (u.kz1 <= u.kz0) rc.fail("adjoint unit without planes", ul, u.kz0);
+            if (g.tma) {
+                // tensor-copy path: the box fits a stage, holds every float of the
+                // unit's cells, and every lane's reads stay inside a box row
+                const int tsb = tma_stage_bytes(g.dxmax, g.dymax);
+                const int nb = tma_boxes(d.dx), W = tma_box_width(d.dx);
+                if (!tma_geometry_ok(d) || d.dx > g.dxmax || d.dy > g.dymax) rc.fail("tensor-copy group member", d.dx, d.dy);
+                if (W > 256 || (8 * W) % 16 != 0) rc.fail("box width", W, 256);
+                if (nb * tma_box_bytes(d.dx, d.dy) > tsb || tsb % 128 != 0) rc.fail("boxes over stage", nb, tsb);
+                const int f0 = tma_first_float(u, d.dx), gx0 = tma_group_of(f0), shift = f0 - 4 * gx0;
+                if (shift < 0 || shift > 3 || 4LL * gx0 > f0) rc.fail("box start", f0, gx0);
+                // every lane's dx voxels lie inside a row of its box (box bx covers the
+                // floats [4 gx0 + 48 dx bx, + 2 W), lanes 16 bx .. of it)
+                for (int lane = 0; lane < kLanes; ++lane) {
+                    const int bx = nb == 1 ? 0 : lane / 16;
+                    const int rel = shift + 3 * d.dx * (lane - 16 * bx);   // floats from the box start
+                    if (rel < 0 || rel + 3 * d.dx > 2 * W) rc.fail("lane reads past box row", lane, rel);
+                    const long long abs0 = 4LL * gx0 + 48LL * d.dx * bx + rel;
+                    if (abs0 != 3LL * d.dx * (u.col0 - kHalo + lane)) rc.fail("lane box offset", lane, abs0);
+                }
+                const int w = tma_warps_per_cta(tsb, kTmaDefaultStages, 0);
+                if ((long long)w * tma_warp_smem(tsb, kTmaDefaultStages) + 128 > kTmaSmemBudget)
+                    rc.fail("tensor-copy shared memory over budget", w, tsb);
+            }
             // a bulk load covers the 16-byte-aligned superset of the row: <= nbytes + 30
-            if (30 + u.nvox * 12 > buf) rc.fail("staging overflow", u.nvox, buf);
+            if (!g.tma && 30 + u.nvox * 12 > buf) rc.fail("staging overflow", u.nvox, buf);
             // unpredicated reads of a specialised spacing: every lane reads dx voxels,
             // inside [0, nvox) or, in a ragged unit, the zeros [nvox, nvox + zv)
-            const bool spec = d.dx <= kMaxSpecializedDx && !g.generic;
+            const bool spec = d.dx <= kMaxSpecializedDx && !g.generic && !g.tma;
             bool ragged = false;
             for (int lane = 0; lane < kLanes; ++lane) {
                 const int cell = u.col0 - kHalo + lane;
@@ -412,7 +506,7 @@ static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecke
             }
             const int zv = imin(d.dx, kLanes * d.dx - u.nvox);
             if (spec && ragged && 15 + 12 * (u.nvox + zv) > buf) rc.fail("zeroed tail overflow", u.nvox + zv, buf);
-            if (warps_per_cta(adj_warp_smem(buf)) * adj_warp_smem(buf) > kSmemBudget)
+            if (!g.tma && warps_per_cta(adj_warp_smem(buf)) * adj_warp_smem(buf) > kSmemBudget)
                 rc.fail("adjoint shared memory over budget", buf, kSmemBudget);
             for (int lane = 0; lane < kLanes; ++lane) {
                 const int cell = u.col0 - kHalo + lane;
@@ -633,7 +727,7 @@ int bsi_selfcheck_ranges(const bsi_instance* inst, int n, int op, int cover, cha
             }
         } else {
             long long ws = 0;
-            const std::vector<Group> groups = plan(descs(inst, n, true), &ws);
+            const std::vector<Group> groups = plan(descs(inst, n, true), &ws, true);
             for (const Group& g : groups) {
                 check_adjoint_group(g, ws, rc, cover != 0);
                 long long total = 0;

@@ -63,6 +63,58 @@ __global__ void __launch_bounds__(kAdjMaxWarps * kLanes, 3)
         for (int s = 0; s < kLoadStages; ++s) mbar_inval(bars + s);
 }
 
+// Tensor-copy path (adjoint_unit_tma): x-spacing <= 8, dy <= 8, X % 4 == 0.
+// One CTA per SM with as many warps as the stage rings fit in shared memory;
+// warp w's ring of b.stages stages of b.buf_bytes sits after its 128 bytes of
+// mbarriers.
+template <int MAXB>
+__global__ void __launch_bounds__(kTmaMaxWarps * kLanes, 1)
+    bsi_adjoint_partials_tma_kernel(const __grid_constant__ Batch<MAXB> b, const __grid_constant__ TmaMaps<MAXB> maps,
+                                    float* __restrict__ part, long long ws_floats) {
+    extern __shared__ __align__(128) unsigned char tsmem[];
+    const int lane = threadIdx.x & (kLanes - 1);
+    const int warp = threadIdx.x >> 5;
+    // tensor copies land on 128-byte boundaries: round the base up (the launch
+    // allocates 128 spare bytes for this)
+    unsigned char* base = tsmem + ((128u - (smem_u32(tsmem) & 127u)) & 127u);
+    unsigned char* wsm = base + (size_t)warp * tma_warp_smem(b.buf_bytes, b.stages);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm);
+    unsigned char* ring = wsm + 128;
+    BSI_GUARD((smem_u32(ring) & 127) == 0 && (b.buf_bytes & 127) == 0 && b.stages >= 1 && b.stages <= kTmaMaxStages,
+              kErrStage, &g_err) {}
+    if (lane == 0) {
+        for (int s = 0; s < b.stages; ++s) mbar_init(bars + s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const int wpc = blockDim.x >> 5;
+    int ii = 0;
+    unsigned q = 0;
+    for (long long r = 0;; ++r) {
+        const long long uu = slot_unit(r, blockIdx.x, warp, gridDim.x, wpc, b.total_units);
+        if (uu < 0) break;
+        while (ii + 1 < b.n && uu >= b.inst[ii + 1].unit_begin) ++ii;
+        const InstDesc& d = b.inst[ii];
+        const void* tm = &maps.m[ii];
+        const long long ul = uu - d.unit_begin;
+        bool ok;
+        switch (d.dx) {
+            case 1: ok = adjoint_unit_tma<1>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            case 2: ok = adjoint_unit_tma<2>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            case 3: ok = adjoint_unit_tma<3>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            case 4: ok = adjoint_unit_tma<4>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            case 5: ok = adjoint_unit_tma<5>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            case 6: ok = adjoint_unit_tma<6>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            case 7: ok = adjoint_unit_tma<7>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            default: ok = adjoint_unit_tma<8>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+        }
+        if (!ok) break;  // a lost box: the error word says so; stop this warp
+    }
+    __syncwarp();
+    if (lane == 0)
+        for (int s = 0; s < b.stages; ++s) mbar_inval(bars + s);
+}
+
 // One thread per stored control point of every instance.  The units that
 // cover point (gx, gy, gz): x-group gx / 29 (columns are complete within a
 // unit), tile-rows jy = gy - m for m = 0..3, and the tile-plane chunks whose
@@ -158,6 +210,34 @@ cudaError_t launch_adjoint_partials(const Batch<MAXB>& b, bool generic, float* p
                    : launch_part_t<MAXB, false>(b, part, ws_floats, s, info);
 }
 
+// Warps per CTA of the tensor-copy kernel: as many as the rings fit in one
+// SM's shared memory (<= kTmaMaxWarps), at most `req` when that is set.
+int tma_warps_per_cta(int stage_bytes, int stages, int req) {
+    int w = (kTmaSmemBudget - 128) / tma_warp_smem(stage_bytes, stages);
+    if (w > kTmaMaxWarps) w = kTmaMaxWarps;
+    if (req > 0 && req < w) w = req;
+    return w < 1 ? 1 : w;
+}
+
+template <int MAXB>
+cudaError_t launch_adjoint_partials_tma(const Batch<MAXB>& b, const TmaMaps<MAXB>& maps, float* part,
+                                        long long ws_floats, cudaStream_t s, LaunchInfo* info) {
+    auto kern = bsi_adjoint_partials_tma_kernel<MAXB>;
+    const int wpc = tma_warps_per_cta(b.buf_bytes, b.stages, b.warps_req);
+    const int threads = wpc * kLanes;
+    const int smem = wpc * tma_warp_smem(b.buf_bytes, b.stages) + 128;
+    KernelFacts f;
+    cudaError_t e = kernel_facts(reinterpret_cast<const void*>(kern), threads, smem, &f);
+    if (e != cudaSuccess) return e;
+    const long long want = cdiv(b.total_units, wpc);
+    const long long cap = (long long)f.sms * f.ctas_per_sm;
+    const int grid = (int)(want < cap ? want : cap);
+    if (info) *info = LaunchInfo{grid, threads, smem, f.ctas_per_sm};
+    if (grid <= 0) return cudaSuccess;
+    kern<<<grid, threads, smem, s>>>(b, maps, part, ws_floats);
+    return cudaGetLastError();
+}
+
 template <int MAXB>
 cudaError_t launch_adjoint_reduce(const Batch<MAXB>& b, const float* part, long long ws_floats, cudaStream_t s,
                                   LaunchInfo* info) {
@@ -177,6 +257,10 @@ cudaError_t launch_adjoint_reduce(const Batch<MAXB>& b, const float* part, long 
 template cudaError_t launch_adjoint_partials<1>(const Batch<1>&, bool, float*, long long, cudaStream_t, LaunchInfo*);
 template cudaError_t launch_adjoint_partials<kMaxBatch>(const Batch<kMaxBatch>&, bool, float*, long long,
                                                          cudaStream_t, LaunchInfo*);
+template cudaError_t launch_adjoint_partials_tma<1>(const Batch<1>&, const TmaMaps<1>&, float*, long long,
+                                                    cudaStream_t, LaunchInfo*);
+template cudaError_t launch_adjoint_partials_tma<kMaxBatch>(const Batch<kMaxBatch>&, const TmaMaps<kMaxBatch>&,
+                                                            float*, long long, cudaStream_t, LaunchInfo*);
 template cudaError_t launch_adjoint_reduce<1>(const Batch<1>&, const float*, long long, cudaStream_t, LaunchInfo*);
 template cudaError_t launch_adjoint_reduce<kMaxBatch>(const Batch<kMaxBatch>&, const float*, long long,
                                                        cudaStream_t, LaunchInfo*);

@@ -114,6 +114,18 @@ __device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t
                  :: "r"(smem_u32(sdst)), "l"(gsrc), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
+// Tiled tensor copy (TMA) of one box of a 3-D tensor map into shared memory
+// at sdst (128-byte aligned), completing on bar with the box's full byte count
+// (parts of the box outside the tensor arrive as zeros).  tmap is the generic
+// address of a CUtensorMap held in kernel parameter space; the innermost
+// coordinate c0 times the element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tensor_load_3d(void* sdst, const void* tmap, int c0, int c1, int c2, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];"
+        :: "r"(smem_u32(sdst)), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)) : "memory");
+}
+
 // One bounded wait round: the thread may sleep up to kSuspendHintNs for the
 // phase of `parity` to complete (it wakes when it does); true if it completed.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {

@@ -59,7 +59,7 @@ struct Batch {
     int n;
     int buf_bytes;          // bytes of one staging row slot (stage_buf_bytes of the largest dx)
     int warps_req;          // requested warps per CTA (0: as many as shared memory allows, <= 8)
-    int reserved;
+    int stages;             // adjoint tensor-copy path: ring stages per warp (else 0)
     long long total_units;
     long long total_points;
     InstDesc inst[MAXB];
@@ -187,6 +187,40 @@ constexpr int kLoadStages = 4;    // adjoint: ring of staging buffers per warp (
 // mbarrier slot per stage, then the load ring.
 BSI_HD int fwd_warp_smem(int buf_bytes) { return kStoreStages * buf_bytes; }
 BSI_HD int adj_warp_smem(int buf_bytes) { return kLoadStages * (16 + buf_bytes); }
+
+// ---------------------------------------------------------------- adjoint, tensor-copy path
+//
+// When the voxel gradient's rows are 16-byte multiples (X % 4 == 0) and the
+// spacing is small (dx, dy <= 8), the adjoint fetches each voxel plane of a
+// unit -- the dy rows of its tile-row, 32 tiles wide -- with TMA tensor copies
+// from a 3-D view of the gradient as 8-byte elements (pairs of floats):
+// (3X/2, Y, Z).  A box row is one contiguous run of the row (<= 256 elements
+// per box dimension): one box of 48 dx + 2 elements for dx <= 5, else two boxes
+// of 24 dx + 2 elements, lanes 0..15 reading the first and 16..31 the second.
+// The first box starts at the 16-byte group holding the unit's first float,
+// which may lie before the array: elements outside it arrive as zeros.
+BSI_HD int tma_boxes(int dx) { return dx <= 5 ? 1 : 2; }
+BSI_HD int tma_box_width(int dx) { return tma_boxes(dx) == 1 ? 48 * dx + 2 : 24 * dx + 2; }
+// Shared bytes of one box of dy rows, padded to the 128 bytes a tensor copy's
+// destination is aligned to.
+BSI_HD int tma_box_bytes(int dx, int dy) { return (8 * tma_box_width(dx) * dy + 127) & ~127; }
+// One ring stage: room for the boxes of any spacing up to (dxmax, dymax).
+BSI_HD int tma_stage_bytes(int dxmax, int dymax) {
+    int m = 0;
+    for (int dx = 1; dx <= dxmax; ++dx) m = imax(m, tma_boxes(dx) * tma_box_bytes(dx, dymax));
+    return m;
+}
+// Shared memory of one warp: 128 bytes of mbarriers, then the ring of stages.
+BSI_HD int tma_warp_smem(int stage_bytes, int stages) { return 128 + stages * stage_bytes; }
+constexpr int kTmaMaxDy = 8;
+constexpr int kTmaMaxStages = 4;
+constexpr int kTmaDefaultStages = 2;
+constexpr int kTmaMaxWarps = 12;                 // register budget: 12 warps x 32 x 170 <= 65536
+constexpr int kTmaSmemBudget = 227 * 1024;       // one CTA per SM takes all of its shared memory
+
+// Float index (x * 3 + channel) of the unit's first float and its 16-byte group.
+BSI_HD int tma_first_float(const AdjUnit& u, int dx) { return (u.col0 - kHalo) * 3 * dx; }
+BSI_HD int tma_group_of(int f) { return f >= 0 ? f / 4 : -((-f + 3) / 4); }   // floor(f / 4)
 
 constexpr int kMaxWarpsPerCta = 8;
 constexpr int kAdjWarpsMax = 4;   // adjoint partials kernel: 4-warp CTAs (register budget)

@@ -525,4 +525,133 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
     return true;
 }
 
+// One adjoint unit on the tensor-copy path (see tma_boxes): voxel plane p of
+// the unit arrives as one or two boxes of dy rows in ring stage
+// (q0 + p) % stages, issued `stages` planes ahead by lane 0; a warp waits once
+// per plane.  Halo, cut and empty tiles read the zeros the copy
+// fills in outside the array, so every lane runs the same unpredicated code.
+// Sums are the same as adjoint_unit's, in the same order.
+template <int DX>
+__device__ __forceinline__ bool adjoint_unit_tma(const InstDesc& d, const void* tmap, long long ul,
+                                                 uint64_t* bars, unsigned char* ring, int stage_bytes, int stages,
+                                                 int lane, unsigned& q, float* part, long long ws_floats,
+                                                 unsigned* err) {
+    const AdjUnit u = adj_unit(d, ul);
+    constexpr int NB = DX <= 5 ? 1 : 2;                     // tma_boxes(DX)
+    constexpr int W = NB == 1 ? 48 * DX + 2 : 24 * DX + 2;  // tma_box_width(DX), 8-byte elements
+    constexpr int row_bytes = 8 * W;
+    const int box_pad = (row_bytes * d.dy + 127) & ~127;    // tma_box_bytes(DX, dy)
+    const int f0 = tma_first_float(u, DX);
+    const int gx0 = tma_group_of(f0);
+    const int shift = f0 - 4 * gx0;                         // 0..3 floats
+    const int y0 = u.jy * d.dy, yn = imin(d.dy, d.Y - y0);
+    const int zb = u.kz0 * d.dz;
+    const int planes = imin(u.kz1 * d.dz, d.Z) - zb;
+    const uint32_t plane_bytes = (uint32_t)(NB * row_bytes * d.dy);
+    const int wyb = weight_base(d.dy), wzb = weight_base(d.dz);
+    const unsigned q0 = q;
+    BSI_GUARD(NB * box_pad <= stage_bytes && shift + 3 * DX * (kLanes / NB) <= 2 * W, kErrStage, err) {}
+
+    int ip = 0;   // producer (lane 0): next plane to put in flight
+    auto issue = [&]() {
+        const unsigned st = (q0 + (unsigned)ip) % (unsigned)stages;
+        mbar_arrive_expect_tx(&bars[st], plane_bytes);
+#pragma unroll
+        for (int bx = 0; bx < NB; ++bx)   // box bx starts 48 DX floats (24 DX elements) after box bx - 1
+            tensor_load_3d(ring + st * stage_bytes + bx * box_pad, tmap, 2 * gx0 + bx * 24 * DX, y0, zb + ip,
+                           &bars[st]);
+        ++ip;
+    };
+    const int bl = NB == 1 ? 0 : lane >> 4;                // this lane's box
+    const uint32_t lane_off = (uint32_t)(bl * box_pad) + 4u * (uint32_t)shift + 12u * DX * (uint32_t)(lane - 16 * bl);
+    if (lane == 0)
+        while (ip < planes && ip < stages) issue();
+
+    float hz[4][4][3];
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) hz[n][m][c] = 0.f;
+
+    int p = 0;
+    for (int kz = u.kz0; kz < u.kz1; ++kz) {
+        const int z0 = kz * d.dz, zn = imin(d.dz, d.Z - z0);
+        for (int rz = 0; rz < zn; ++rz, ++p) {
+            const unsigned qq = q0 + (unsigned)p;
+            const unsigned st = qq % (unsigned)stages;
+            if (!mbar_wait_bounded(&bars[st], (qq / (unsigned)stages) & 1u)) {
+                // a box never completed: record it, give the boxes still in
+                // flight a bounded chance to land, and stop this warp
+                if (lane == 0) atomicOr(err, kErrTimeout);
+                for (int pp = p + 1; pp < planes && pp < p + stages; ++pp) {
+                    const unsigned qp = q0 + (unsigned)pp;
+                    (void)mbar_wait_bounded(&bars[qp % (unsigned)stages], (qp / (unsigned)stages) & 1u);
+                }
+                q = q0 + (unsigned)planes;
+                return false;
+            }
+            // shared address of this lane's first voxel in row 0 of its box
+            const uint32_t sv = smem_u32(ring + st * stage_bytes) + lane_off;
+            float hy[4][3];
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) hy[m][c] = 0.f;
+            for (int ry = 0; ry < yn; ++ry) {
+                float q4[4][3];
+#pragma unroll
+                for (int l = 0; l < 4; ++l)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) q4[l][c] = 0.f;
+                // 16-byte loads for DX = 4, 8: shift is then 0, box rows are 16-byte multiples
+                gather_tile<DX, DX % 4 == 0 ? 4 : 1>(q4, sv + (uint32_t)(ry * row_bytes));
+                const float b0 = c_lut.w[wyb + 4 * ry], b1 = c_lut.w[wyb + 4 * ry + 1];
+                const float b2 = c_lut.w[wyb + 4 * ry + 2], b3 = c_lut.w[wyb + 4 * ry + 3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float h = q4[0][c] + __shfl_up_sync(kFull, q4[1][c], 1) +
+                                    __shfl_up_sync(kFull, q4[2][c], 2) + __shfl_up_sync(kFull, q4[3][c], 3);
+                    hy[0][c] = fmaf(b0, h, hy[0][c]);
+                    hy[1][c] = fmaf(b1, h, hy[1][c]);
+                    hy[2][c] = fmaf(b2, h, hy[2][c]);
+                    hy[3][c] = fmaf(b3, h, hy[3][c]);
+                }
+            }
+            // the stage may be refilled once every lane has read it
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0 && ip < planes) issue();
+            const float a0 = c_lut.w[wzb + 4 * rz], a1 = c_lut.w[wzb + 4 * rz + 1];
+            const float a2 = c_lut.w[wzb + 4 * rz + 2], a3 = c_lut.w[wzb + 4 * rz + 3];
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    hz[0][m][c] = fmaf(a0, hy[m][c], hz[0][m][c]);
+                    hz[1][m][c] = fmaf(a1, hy[m][c], hz[1][m][c]);
+                    hz[2][m][c] = fmaf(a2, hy[m][c], hz[2][m][c]);
+                    hz[3][m][c] = fmaf(a3, hy[m][c], hz[3][m][c]);
+                }
+        }
+        flush_plane(d, ul, kz - u.kz0, u, lane, hz[0], part, ws_floats, err);
+#pragma unroll
+        for (int n = 0; n < 3; ++n)
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) hz[n][m][c] = hz[n + 1][m][c];
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) hz[3][m][c] = 0.f;
+    }
+    const int nk = u.kz1 - u.kz0;
+#pragma unroll
+    for (int n = 0; n < 3; ++n) flush_plane(d, ul, nk + n, u, lane, hz[n], part, ws_floats, err);
+    q = q0 + (unsigned)planes;
+    return true;
+}
+
 }  // namespace bsi

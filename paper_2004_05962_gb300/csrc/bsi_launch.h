@@ -2,6 +2,7 @@
 // kernel translation units (bsi_forward.cu, bsi_adjoint.cu).
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the type only: maps are encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
 #include "bsi_geometry.h"
@@ -23,6 +24,19 @@ cudaError_t launch_forward(const Batch<MAXB>& b, bool bf16, bool generic, cudaSt
 template <int MAXB>
 cudaError_t launch_adjoint_partials(const Batch<MAXB>& b, bool generic, float* part,
                                     long long ws_floats, cudaStream_t s, LaunchInfo* info);
+
+// Tensor maps of the voxel gradients of a batch on the adjoint's tensor-copy
+// path (one per instance, a kernel parameter).
+template <int MAXB>
+struct TmaMaps {
+    CUtensorMap m[MAXB];
+};
+
+int tma_warps_per_cta(int stage_bytes, int stages, int req);
+
+template <int MAXB>
+cudaError_t launch_adjoint_partials_tma(const Batch<MAXB>& b, const TmaMaps<MAXB>& maps, float* part,
+                                        long long ws_floats, cudaStream_t s, LaunchInfo* info);
 
 template <int MAXB>
 cudaError_t launch_adjoint_reduce(const Batch<MAXB>& b, const float* part, long long ws_floats,
