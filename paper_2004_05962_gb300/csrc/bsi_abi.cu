@@ -144,6 +144,7 @@ static void fill_desc(InstDesc& d, const bsi_geom& g, bool adjoint, bool bf16 = 
         d.units = (long long)d.ncz * d.ncy * d.nxg;
     } else {
         d.zchunk = zchunk;
+        d.tma_rows = tma_block_rows(d.dx, d.dy);
         d.nxg = empty ? 0 : (int)cdiv(d.nx, kGroupCells);
         d.nzc = empty ? 0 : (int)cdiv(d.ncz, zchunk);
         d.units = (long long)d.nzc * d.ncy * d.nxg;
@@ -160,7 +161,7 @@ struct Group {
     bool generic = false;
     bool tma = false;    // adjoint tensor-copy path
     int dxmax = 1;
-    int dymax = 1;
+    int tma_stage = 0;   // tensor-copy path: bytes of one ring stage (largest block of its instances)
     int warps_req = 0;   // smallest non-zero warps_per_cta request of its instances
     std::vector<InstDesc> inst;
 };
@@ -168,9 +169,9 @@ struct Group {
 static bool misaligned(const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) != 0; }
 
 // Whether an adjoint instance can take the tensor-copy path: rows of 16-byte
-// multiples in a 16-byte-aligned array, a box of <= 8 rows and x-spacing <= 8.
+// multiples in a 16-byte-aligned array and x-spacing <= 8.
 static bool tma_geometry_ok(const InstDesc& d) {
-    return d.units > 0 && d.dx <= kMaxSpecializedDx && d.dy <= kTmaMaxDy && d.X % 4 == 0 && !misaligned(d.grad, 16);
+    return d.units > 0 && d.dx <= kMaxSpecializedDx && d.X % 4 == 0 && !misaligned(d.grad, 16);
 }
 
 // Splits instances into groups of one kernel variant, in caller order, at most
@@ -195,13 +196,13 @@ static std::vector<Group> plan(const std::vector<InstDesc>& all, long long* ws_f
             off += adj_floats(d);
             cur.inst.push_back(d);
             cur.dxmax = std::max(cur.dxmax, d.dx);
-            cur.dymax = std::max(cur.dymax, d.dy);
+            if (tma) cur.tma_stage = std::max(cur.tma_stage, tma_block_bytes(d.dx, d.tma_rows));
             if (d.warps_req > 0 && (cur.warps_req == 0 || d.warps_req < cur.warps_req)) cur.warps_req = d.warps_req;
             if ((int)cur.inst.size() == kMaxBatch) {
                 out.push_back(cur);
                 cur.inst.clear();
                 cur.dxmax = 1;
-                cur.dymax = 1;
+                cur.tma_stage = 0;
                 cur.warps_req = 0;
             }
         }
@@ -224,8 +225,8 @@ template <int MAXB>
 static void to_batch(const Group& g, Batch<MAXB>& b) {
     std::memset(&b, 0, sizeof b);
     b.n = (int)g.inst.size();
-    b.buf_bytes = g.tma ? tma_stage_bytes(g.dxmax, g.dymax) : stage_buf_bytes(g.dxmax);
-    b.stages = g.tma ? kTmaDefaultStages : 0;
+    b.buf_bytes = g.tma ? g.tma_stage : stage_buf_bytes(g.dxmax);
+    b.stages = g.tma ? tma_default_stages(g.tma_stage) : 0;
     b.warps_req = g.tma ? 0 : g.warps_req;
     for (int i = 0; i < b.n; ++i) {
         b.inst[i] = g.inst[i];
@@ -252,13 +253,14 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // The gradient of one instance as a 3-D tensor of 8-byte elements (float
-// pairs): (3X/2, Y, Z), with a box of (tma_box_width(dx), dy, 1); zeros outside.
+// pairs): (3X/2, Y, Z), with a box of (tma_box_width(dx), tma_rows, 1); zeros
+// outside.
 static cudaError_t encode_grad_map(const InstDesc& d, CUtensorMap* m) {
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
     const cuuint64_t dims[3] = {(cuuint64_t)d.X * 3 / 2, (cuuint64_t)d.Y, (cuuint64_t)d.Z};
     const cuuint64_t strides[2] = {(cuuint64_t)d.X * 12, (cuuint64_t)d.X * 12 * (cuuint64_t)d.Y};
-    const cuuint32_t box[3] = {(cuuint32_t)tma_box_width(d.dx), (cuuint32_t)d.dy, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)tma_box_width(d.dx), (cuuint32_t)d.tma_rows, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float*>(d.grad), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -473,11 +475,12 @@ static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecke
             if (g.tma) {
                 // tensor-copy path: the box fits a stage, holds every float of the
                 // unit's cells, and every lane's reads stay inside a box row
-                const int tsb = tma_stage_bytes(g.dxmax, g.dymax);
+                const int tsb = g.tma_stage, rb = d.tma_rows;
                 const int nb = tma_boxes(d.dx), W = tma_box_width(d.dx);
-                if (!tma_geometry_ok(d) || d.dx > g.dxmax || d.dy > g.dymax) rc.fail("tensor-copy group member", d.dx, d.dy);
+                if (!tma_geometry_ok(d) || d.dx > g.dxmax) rc.fail("tensor-copy group member", d.dx, d.dy);
+                if (rb < 1 || rb > kTmaMaxRows || d.dy % rb != 0) rc.fail("rows per block", rb, d.dy);
                 if (W > 256 || (8 * W) % 16 != 0) rc.fail("box width", W, 256);
-                if (nb * tma_box_bytes(d.dx, d.dy) > tsb || tsb % 128 != 0) rc.fail("boxes over stage", nb, tsb);
+                if (tma_block_bytes(d.dx, rb) > tsb || tsb % 128 != 0) rc.fail("block over stage", rb, tsb);
                 const int f0 = tma_first_float(u, d.dx), gx0 = tma_group_of(f0), shift = f0 - 4 * gx0;
                 if (shift < 0 || shift > 3 || 4LL * gx0 > f0) rc.fail("box start", f0, gx0);
                 // every lane's dx voxels lie inside a row of its box (box bx covers the
@@ -489,8 +492,9 @@ static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecke
                     const long long abs0 = 4LL * gx0 + 48LL * d.dx * bx + rel;
                     if (abs0 != 3LL * d.dx * (u.col0 - kHalo + lane)) rc.fail("lane box offset", lane, abs0);
                 }
-                const int w = tma_warps_per_cta(tsb, kTmaDefaultStages, 0);
-                if ((long long)w * tma_warp_smem(tsb, kTmaDefaultStages) + 128 > kTmaSmemBudget)
+                const int st = tma_default_stages(tsb);
+                const int w = tma_warps_per_cta(tsb, st, 0);
+                if (st < kTmaMinStages || st > kTmaMaxStages || (long long)w * tma_warp_smem(tsb, st) + 128 > kTmaSmemBudget)
                     rc.fail("tensor-copy shared memory over budget", w, tsb);
             }
             // a bulk load covers the 16-byte-aligned superset of the row: <= nbytes + 30

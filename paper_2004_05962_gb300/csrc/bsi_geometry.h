@@ -43,7 +43,7 @@ struct InstDesc {
     int zchunk;          // adjoint: tile-planes per chunk
     int gcells;          // forward: tiles per warp strip (<= 29; see fwd_strip_tiles)
     int warps_req;       // requested warps per CTA from the tile-config table (0: automatic)
-    int reserved;
+    int tma_rows;        // adjoint tensor-copy path: rows per block (tma_block_rows), else 0
     long long units;        // units of this instance
     long long unit_begin;   // first global unit index of this instance in its launch
     long long point_begin;  // adjoint reduce: first global grid point of this instance
@@ -190,33 +190,46 @@ BSI_HD int adj_warp_smem(int buf_bytes) { return kLoadStages * (16 + buf_bytes);
 
 // ---------------------------------------------------------------- adjoint, tensor-copy path
 //
-// When the voxel gradient's rows are 16-byte multiples (X % 4 == 0) and the
-// spacing is small (dx, dy <= 8), the adjoint fetches each voxel plane of a
-// unit -- the dy rows of its tile-row, 32 tiles wide -- with TMA tensor copies
-// from a 3-D view of the gradient as 8-byte elements (pairs of floats):
-// (3X/2, Y, Z).  A box row is one contiguous run of the row (<= 256 elements
-// per box dimension): one box of 48 dx + 2 elements for dx <= 5, else two boxes
-// of 24 dx + 2 elements, lanes 0..15 reading the first and 16..31 the second.
+// When the voxel gradient's rows are 16-byte multiples (X % 4 == 0) and
+// dx <= 8, the adjoint fetches its input with TMA tensor copies from a 3-D
+// view of the gradient as 8-byte elements (pairs of floats): (3X/2, Y, Z).
+// One ring stage holds a BLOCK: rb consecutive rows of a voxel plane of the
+// unit's tile-row, 32 tiles wide (rb divides dy, so a plane is dy / rb blocks).
+// A box row is one contiguous run of a gradient row (<= 256 elements per box
+// dimension): one box of 48 dx + 2 elements for dx <= 5, else two boxes of
+// 24 dx + 2 elements, lanes 0..15 reading the first and 16..31 the second.
 // The first box starts at the 16-byte group holding the unit's first float,
 // which may lie before the array: elements outside it arrive as zeros.
 BSI_HD int tma_boxes(int dx) { return dx <= 5 ? 1 : 2; }
 BSI_HD int tma_box_width(int dx) { return tma_boxes(dx) == 1 ? 48 * dx + 2 : 24 * dx + 2; }
-// Shared bytes of one box of dy rows, padded to the 128 bytes a tensor copy's
+// Shared bytes of one box of rb rows, padded to the 128 bytes a tensor copy's
 // destination is aligned to.
-BSI_HD int tma_box_bytes(int dx, int dy) { return (8 * tma_box_width(dx) * dy + 127) & ~127; }
-// One ring stage: room for the boxes of any spacing up to (dxmax, dymax).
-BSI_HD int tma_stage_bytes(int dxmax, int dymax) {
-    int m = 0;
-    for (int dx = 1; dx <= dxmax; ++dx) m = imax(m, tma_boxes(dx) * tma_box_bytes(dx, dymax));
-    return m;
+BSI_HD int tma_box_bytes(int dx, int rb) { return (8 * tma_box_width(dx) * rb + 127) & ~127; }
+BSI_HD int tma_block_bytes(int dx, int rb) { return tma_boxes(dx) * tma_box_bytes(dx, rb); }
+
+constexpr int kTmaMaxRows = 8;                   // rows per block
+constexpr int kTmaBlockTarget = 14 * 1024;       // largest block that still leaves room for 2 stages x 8 warps
+constexpr int kTmaMinStages = 2;
+constexpr int kTmaMaxStages = 4;
+constexpr int kTmaMaxWarps = 12;                 // register budget: 12 warps x 32 x 170 <= 65536
+constexpr int kTmaSmemBudget = 227 * 1024;       // one CTA per SM takes all of its shared memory
+
+// Rows per block for spacing (dx, dy): the largest divisor of dy up to
+// kTmaMaxRows whose block fits kTmaBlockTarget (1 always does).
+BSI_HD int tma_block_rows(int dx, int dy) {
+    for (int rb = imin(dy, kTmaMaxRows); rb > 1; --rb)
+        if (dy % rb == 0 && tma_block_bytes(dx, rb) <= kTmaBlockTarget) return rb;
+    return 1;
 }
 // Shared memory of one warp: 128 bytes of mbarriers, then the ring of stages.
 BSI_HD int tma_warp_smem(int stage_bytes, int stages) { return 128 + stages * stage_bytes; }
-constexpr int kTmaMaxDy = 8;
-constexpr int kTmaMaxStages = 4;
-constexpr int kTmaDefaultStages = 2;
-constexpr int kTmaMaxWarps = 12;                 // register budget: 12 warps x 32 x 170 <= 65536
-constexpr int kTmaSmemBudget = 227 * 1024;       // one CTA per SM takes all of its shared memory
+// Default ring depth for a stage size: as deep as fits beside 12 warps, 2..3
+// (measured: a 4th stage slowed small blocks down; 3 beat 2 where both fit).
+constexpr int kTmaDefaultMaxStages = 3;
+BSI_HD int tma_default_stages(int stage_bytes) {
+    const int s = ((kTmaSmemBudget - 128) / kTmaMaxWarps - 128) / stage_bytes;
+    return s < kTmaMinStages ? kTmaMinStages : (s > kTmaDefaultMaxStages ? kTmaDefaultMaxStages : s);
+}
 
 // Float index (x * 3 + channel) of the unit's first float and its 16-byte group.
 BSI_HD int tma_first_float(const AdjUnit& u, int dx) { return (u.col0 - kHalo) * 3 * dx; }

@@ -525,12 +525,12 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
     return true;
 }
 
-// One adjoint unit on the tensor-copy path (see tma_boxes): voxel plane p of
-// the unit arrives as one or two boxes of dy rows in ring stage
-// (q0 + p) % stages, issued `stages` planes ahead by lane 0; a warp waits once
-// per plane.  Halo, cut and empty tiles read the zeros the copy
-// fills in outside the array, so every lane runs the same unpredicated code.
-// Sums are the same as adjoint_unit's, in the same order.
+// One adjoint unit on the tensor-copy path (see tma_boxes): block k of the
+// unit (rows [i rb, i rb + rb) of voxel plane p, k = p * nblk + i) arrives as
+// one or two boxes in ring stage (q0 + k) % stages, issued `stages` blocks
+// ahead by lane 0; a warp waits once per block.  Halo, cut and empty tiles read
+// the zeros the copy fills in outside the array, so every lane runs the same
+// unpredicated code.  Rows are summed in the same order as adjoint_unit.
 template <int DX>
 __device__ __forceinline__ bool adjoint_unit_tma(const InstDesc& d, const void* tmap, long long ul,
                                                  uint64_t* bars, unsigned char* ring, int stage_bytes, int stages,
@@ -540,32 +540,41 @@ __device__ __forceinline__ bool adjoint_unit_tma(const InstDesc& d, const void* 
     constexpr int NB = DX <= 5 ? 1 : 2;                     // tma_boxes(DX)
     constexpr int W = NB == 1 ? 48 * DX + 2 : 24 * DX + 2;  // tma_box_width(DX), 8-byte elements
     constexpr int row_bytes = 8 * W;
-    const int box_pad = (row_bytes * d.dy + 127) & ~127;    // tma_box_bytes(DX, dy)
+    const int rb = d.tma_rows;
+    const int box_pad = (row_bytes * rb + 127) & ~127;      // tma_box_bytes(DX, rb)
     const int f0 = tma_first_float(u, DX);
     const int gx0 = tma_group_of(f0);
     const int shift = f0 - 4 * gx0;                         // 0..3 floats
     const int y0 = u.jy * d.dy, yn = imin(d.dy, d.Y - y0);
+    const int nblk = (yn + rb - 1) / rb;                    // blocks per voxel plane of this tile-row
     const int zb = u.kz0 * d.dz;
     const int planes = imin(u.kz1 * d.dz, d.Z) - zb;
-    const uint32_t plane_bytes = (uint32_t)(NB * row_bytes * d.dy);
+    const int blocks = planes * nblk;
+    const uint32_t block_bytes = (uint32_t)(NB * row_bytes * rb);
     const int wyb = weight_base(d.dy), wzb = weight_base(d.dz);
     const unsigned q0 = q;
-    BSI_GUARD(NB * box_pad <= stage_bytes && shift + 3 * DX * (kLanes / NB) <= 2 * W, kErrStage, err) {}
+    BSI_GUARD(rb >= 1 && rb <= kTmaMaxRows && NB * box_pad <= stage_bytes && shift + 3 * DX * (kLanes / NB) <= 2 * W,
+              kErrStage, err) {}
 
-    int ip = 0;   // producer (lane 0): next plane to put in flight
+    // producer (lane 0): next block to put in flight, as (plane, block in plane)
+    int ik = 0, ip = 0, ii = 0;
     auto issue = [&]() {
-        const unsigned st = (q0 + (unsigned)ip) % (unsigned)stages;
-        mbar_arrive_expect_tx(&bars[st], plane_bytes);
+        const unsigned st = (q0 + (unsigned)ik) % (unsigned)stages;
+        mbar_arrive_expect_tx(&bars[st], block_bytes);
 #pragma unroll
         for (int bx = 0; bx < NB; ++bx)   // box bx starts 48 DX floats (24 DX elements) after box bx - 1
-            tensor_load_3d(ring + st * stage_bytes + bx * box_pad, tmap, 2 * gx0 + bx * 24 * DX, y0, zb + ip,
-                           &bars[st]);
-        ++ip;
+            tensor_load_3d(ring + st * stage_bytes + bx * box_pad, tmap, 2 * gx0 + bx * 24 * DX, y0 + ii * rb,
+                           zb + ip, &bars[st]);
+        ++ik;
+        if (++ii == nblk) {
+            ii = 0;
+            ++ip;
+        }
     };
+    if (lane == 0)
+        while (ik < blocks && ik < stages) issue();
     const int bl = NB == 1 ? 0 : lane >> 4;                // this lane's box
     const uint32_t lane_off = (uint32_t)(bl * box_pad) + 4u * (uint32_t)shift + 12u * DX * (uint32_t)(lane - 16 * bl);
-    if (lane == 0)
-        while (ip < planes && ip < stages) issue();
 
     float hz[4][4][3];
 #pragma unroll
@@ -575,54 +584,58 @@ __device__ __forceinline__ bool adjoint_unit_tma(const InstDesc& d, const void* 
 #pragma unroll
             for (int c = 0; c < 3; ++c) hz[n][m][c] = 0.f;
 
-    int p = 0;
+    int k = 0;
     for (int kz = u.kz0; kz < u.kz1; ++kz) {
         const int z0 = kz * d.dz, zn = imin(d.dz, d.Z - z0);
-        for (int rz = 0; rz < zn; ++rz, ++p) {
-            const unsigned qq = q0 + (unsigned)p;
-            const unsigned st = qq % (unsigned)stages;
-            if (!mbar_wait_bounded(&bars[st], (qq / (unsigned)stages) & 1u)) {
-                // a box never completed: record it, give the boxes still in
-                // flight a bounded chance to land, and stop this warp
-                if (lane == 0) atomicOr(err, kErrTimeout);
-                for (int pp = p + 1; pp < planes && pp < p + stages; ++pp) {
-                    const unsigned qp = q0 + (unsigned)pp;
-                    (void)mbar_wait_bounded(&bars[qp % (unsigned)stages], (qp / (unsigned)stages) & 1u);
-                }
-                q = q0 + (unsigned)planes;
-                return false;
-            }
-            // shared address of this lane's first voxel in row 0 of its box
-            const uint32_t sv = smem_u32(ring + st * stage_bytes) + lane_off;
+        for (int rz = 0; rz < zn; ++rz) {
             float hy[4][3];
 #pragma unroll
             for (int m = 0; m < 4; ++m)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) hy[m][c] = 0.f;
-            for (int ry = 0; ry < yn; ++ry) {
-                float q4[4][3];
-#pragma unroll
-                for (int l = 0; l < 4; ++l)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) q4[l][c] = 0.f;
-                // 16-byte loads for DX = 4, 8: shift is then 0, box rows are 16-byte multiples
-                gather_tile<DX, DX % 4 == 0 ? 4 : 1>(q4, sv + (uint32_t)(ry * row_bytes));
-                const float b0 = c_lut.w[wyb + 4 * ry], b1 = c_lut.w[wyb + 4 * ry + 1];
-                const float b2 = c_lut.w[wyb + 4 * ry + 2], b3 = c_lut.w[wyb + 4 * ry + 3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float h = q4[0][c] + __shfl_up_sync(kFull, q4[1][c], 1) +
-                                    __shfl_up_sync(kFull, q4[2][c], 2) + __shfl_up_sync(kFull, q4[3][c], 3);
-                    hy[0][c] = fmaf(b0, h, hy[0][c]);
-                    hy[1][c] = fmaf(b1, h, hy[1][c]);
-                    hy[2][c] = fmaf(b2, h, hy[2][c]);
-                    hy[3][c] = fmaf(b3, h, hy[3][c]);
+            for (int i = 0; i < nblk; ++i, ++k) {
+                const unsigned qq = q0 + (unsigned)k;
+                const unsigned st = qq % (unsigned)stages;
+                if (!mbar_wait_bounded(&bars[st], (qq / (unsigned)stages) & 1u)) {
+                    // a block never completed: record it, give the blocks still in
+                    // flight a bounded chance to land, and stop this warp
+                    if (lane == 0) atomicOr(err, kErrTimeout);
+                    for (int kk = k + 1; kk < blocks && kk < k + stages; ++kk) {
+                        const unsigned qp = q0 + (unsigned)kk;
+                        (void)mbar_wait_bounded(&bars[qp % (unsigned)stages], (qp / (unsigned)stages) & 1u);
+                    }
+                    q = q0 + (unsigned)blocks;
+                    return false;
                 }
+                // shared address of this lane's first voxel in row 0 of the block
+                const uint32_t sv = smem_u32(ring + st * stage_bytes) + lane_off;
+                const int ry0 = i * rb, rows = imin(rb, yn - ry0);
+                for (int r = 0; r < rows; ++r) {
+                    const int ry = ry0 + r;
+                    float q4[4][3];
+#pragma unroll
+                    for (int l = 0; l < 4; ++l)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) q4[l][c] = 0.f;
+                    // 16-byte loads for DX = 4, 8: shift is then 0, box rows are 16-byte multiples
+                    gather_tile<DX, DX % 4 == 0 ? 4 : 1>(q4, sv + (uint32_t)(r * row_bytes));
+                    const float b0 = c_lut.w[wyb + 4 * ry], b1 = c_lut.w[wyb + 4 * ry + 1];
+                    const float b2 = c_lut.w[wyb + 4 * ry + 2], b3 = c_lut.w[wyb + 4 * ry + 3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float h = q4[0][c] + __shfl_up_sync(kFull, q4[1][c], 1) +
+                                        __shfl_up_sync(kFull, q4[2][c], 2) + __shfl_up_sync(kFull, q4[3][c], 3);
+                        hy[0][c] = fmaf(b0, h, hy[0][c]);
+                        hy[1][c] = fmaf(b1, h, hy[1][c]);
+                        hy[2][c] = fmaf(b2, h, hy[2][c]);
+                        hy[3][c] = fmaf(b3, h, hy[3][c]);
+                    }
+                }
+                // the stage may be refilled once every lane has read it
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0 && ik < blocks) issue();
             }
-            // the stage may be refilled once every lane has read it
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0 && ip < planes) issue();
             const float a0 = c_lut.w[wzb + 4 * rz], a1 = c_lut.w[wzb + 4 * rz + 1];
             const float a2 = c_lut.w[wzb + 4 * rz + 2], a3 = c_lut.w[wzb + 4 * rz + 3];
 #pragma unroll
@@ -650,7 +663,7 @@ __device__ __forceinline__ bool adjoint_unit_tma(const InstDesc& d, const void* 
     const int nk = u.kz1 - u.kz0;
 #pragma unroll
     for (int n = 0; n < 3; ++n) flush_plane(d, ul, nk + n, u, lane, hz[n], part, ws_floats, err);
-    q = q0 + (unsigned)planes;
+    q = q0 + (unsigned)blocks;
     return true;
 }
 

@@ -106,9 +106,9 @@ def test_adjoint_is_deterministic():
     assert torch.equal(a, b)
 
 
-# The adjoint's tensor-copy path (X % 4 == 0, dx <= 8, dy <= 8, 16-byte-aligned
+# The adjoint's tensor-copy path (X % 4 == 0, dx <= 8, 16-byte-aligned
 # gradient): every x-spacing, ragged y and z tails, dy = 8, several x-groups,
-# X = 4 (a box wider than the array)
+# X = 4 (a box wider than the array), blocks of 1, 4 and 5 rows
 TMA = [
     ((9, 10, 12), (2, 2, 1)),
     ((11, 13, 40), (3, 5, 2)),
@@ -119,12 +119,15 @@ TMA = [
     ((6, 11, 212), (3, 4, 7)),
     ((9, 9, 264), (2, 2, 8)),
     ((20, 21, 4), (5, 5, 5)),
+    ((9, 30, 40), (2, 10, 3)),      # dy = 10: blocks of 5 rows
+    ((7, 25, 48), (3, 11, 4)),      # dy = 11 (prime): blocks of 1 row
+    ((6, 35, 264), (2, 16, 8)),     # dx = 8, dy = 16: two boxes of 4 rows
 ]
 
 
 @pytest.mark.parametrize("shape,spacing", TMA, ids=[f"{s}-{d}" for s, d in TMA])
 def test_adjoint_tensor_copy_path_matches_oracle(shape, spacing):
-    assert shape[2] % 4 == 0 and spacing[2] <= 8 and spacing[1] <= 8
+    assert shape[2] % 4 == 0 and spacing[2] <= 8
     g = synth.normal_field(shape, seed=sum(shape) + 3 * sum(spacing))
     got = gpu_adjoint(g, spacing)
     err, tol = adj_err(got, g, spacing)
