@@ -94,7 +94,10 @@ bsi_status bsi_geom_init(bsi_geom* g, int64_t X, int64_t Y, int64_t Z, int32_t d
 bsi_status bsi_field_forward(const bsi_geom* g, const float* phi, void* field, bsi_dtype out_dtype,
                              bsi_stream_t stream);
 
-/* Workspace bytes bsi_field_adjoint needs for geometry g (0 for an empty volume). */
+/* Workspace bytes bsi_field_adjoint needs for geometry g (0 for an empty
+ * volume): the most any of its launch plans can use, since the tile-planes
+ * per warp unit are chosen per call (from the device's SM count) unless the
+ * tile-config table fixes them. */
 size_t bsi_adjoint_workspace_bytes(const bsi_geom* g);
 
 /* Adjoint BSI: the transpose of Eq. 1 applied to a voxel gradient,
@@ -106,7 +109,10 @@ size_t bsi_adjoint_workspace_bytes(const bsi_geom* g);
  *   workspace  : device scratch of at least bsi_adjoint_workspace_bytes(g)
  *                bytes, 16-byte aligned (BSI_ERR_ALIGN otherwise); contents
  *                on entry are ignored.  May be NULL when the size is 0.
- * Two kernels: per-warp partial sums over tiles, then a fixed-order reduce. */
+ * Two kernels: per-warp partial sums over tiles, then a fixed-order reduce.
+ * A gradient with X % 4 == 0 at a 16-byte-aligned address and dx <= 8 is read
+ * by TMA tensor copies (one per block of rows), any other by one bulk copy per
+ * row; both add the same terms in the same order (bitwise equal results). */
 bsi_status bsi_field_adjoint(const bsi_geom* g, const float* grad_field, float* grad_phi,
                              void* workspace, size_t workspace_bytes, bsi_stream_t stream);
 
@@ -147,9 +153,10 @@ bsi_status bsi_field_adjoint_batched(const bsi_instance* inst, int n, void* work
  *
  * Scratch: a file-scope device array of BSI_NOALLOC_SCRATCH_BYTES (64 MiB)
  * inside the library, held on every device where the library's module is
- * loaded until the process exits.  Volumes whose bsi_adjoint_workspace_bytes
- * exceed it are rejected with BSI_ERR_SCRATCH_LIMIT before anything is
- * enqueued (the 512x512x300 volume at spacing 5 needs about 60 MB).
+ * loaded until the process exits.  The call picks tile-planes per warp unit
+ * among the plans whose partial sums fit it; a volume that no plan fits is
+ * rejected with BSI_ERR_SCRATCH_LIMIT before anything is enqueued (the
+ * 512x512x300 volume at spacing 5 needs 44 to 69 MB depending on the plan).
  * The call allocates no device memory: no cudaMalloc, cudaFree or allocating
  * library routine.  Its first call on a device looks up the array's device
  * address (cudaGetSymbolAddress, once per device, with that device current),
@@ -169,7 +176,8 @@ bsi_status bsi_field_adjoint_noalloc(const bsi_geom* g, const float* grad_field,
  * is data.  A zero field means "library default". */
 typedef struct {
     int32_t dx, dy, dz;        /* spacing the entry applies to; 0 matches any value */
-    int32_t adj_zchunk;        /* adjoint: tile-planes per warp unit, 3..16 (default 4) */
+    int32_t adj_zchunk;        /* adjoint: tile-planes per warp unit, 3..16 (0: chosen per volume
+                                  by the library's load-balance model) */
     int32_t adj_warps;         /* adjoint: warps per CTA, 1..4 (default 4, fewer if shared
                                   memory requires) */
     int32_t fwd_strip_tiles;   /* forward: tiles per warp strip, 4..29 (default 28 or 29,
@@ -189,7 +197,9 @@ typedef struct {
 bsi_status bsi_set_tile_configs(const bsi_tile_config* cfgs, int n);
 
 /* The launch shape the library will use for spacing (dx, dy, dz), defaults
- * filled in; BSI_ERR_NULL if out is NULL, BSI_ERR_SPACING for a bad spacing. */
+ * filled in except adj_zchunk and fwd_strip_tiles, which stay 0 when unset
+ * because they depend on the volume; BSI_ERR_NULL if out is NULL,
+ * BSI_ERR_SPACING for a bad spacing. */
 bsi_status bsi_get_tile_config(int32_t dx, int32_t dy, int32_t dz, bsi_tile_config* out);
 
 /* Static string naming a status code. */

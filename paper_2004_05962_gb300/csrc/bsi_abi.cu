@@ -68,10 +68,13 @@ cudaError_t kernel_facts(const void* kernel, int threads, int smem, KernelFacts*
 
 // ----------------------------------------------------------- planning
 
-// Tile-planes per adjoint unit.  Must be >= 3: the reduce kernel then finds
-// every grid plane in at most two consecutive chunks.
-constexpr int kDefaultZChunk = 4;
-static_assert(kDefaultZChunk >= 3, "adjoint reduce assumes chunks of at least 3 tile-planes");
+// Tile-planes per adjoint unit: kMinZChunk..kMaxZChunk, chosen per volume by
+// choose_zchunk unless the tile-config table fixes it.  Must be >= 3: the
+// reduce kernel then finds every grid plane in at most two consecutive chunks.
+constexpr int kMinZChunk = 3;
+constexpr int kMaxZChunk = 16;
+constexpr int kDefaultZChunk = 4;   // where no model applies (empty volumes, workspace queries)
+static_assert(kMinZChunk >= 3, "adjoint reduce assumes chunks of at least 3 tile-planes");
 
 static thread_local char t_cuda_msg[256] = "";
 
@@ -151,9 +154,97 @@ static void fill_desc(InstDesc& d, const bsi_geom& g, bool adjoint, bool bf16 = 
     }
 }
 
+static void set_zchunk(InstDesc& d, int zc) {
+    d.zchunk = zc;
+    d.nzc = d.ncz > 0 ? (int)cdiv(d.ncz, zc) : 0;
+    d.units = (long long)d.nzc * d.ncy * d.nxg;
+}
+
 static long long adj_floats(const InstDesc& d) {
     const long long f = d.units * adj_unit_floats(d);
     return (f + 3) & ~3LL;  // keep every instance's partials 16-byte aligned
+}
+
+// Workspace floats an adjoint instance may need: for the table's zchunk if it
+// fixes one, else the most (least, with `least`) over every zchunk
+// choose_zchunk may pick.
+static long long adj_floats_bound(const bsi_geom& g, bool least = false) {
+    InstDesc d;
+    fill_desc(d, g, true);
+    if (lookup_config(g.dx, g.dy, g.dz).adj_zchunk > 0) return adj_floats(d);
+    long long m = -1;
+    for (int zc = kMinZChunk; zc <= kMaxZChunk; ++zc) {
+        set_zchunk(d, zc);
+        const long long f = adj_floats(d);
+        if (m < 0 || (least ? f < m : f > m)) m = f;
+    }
+    return m;
+}
+
+// SM count of the current device, cached per device (152, a GB300's, when no
+// device can be queried: the host-only self-check).
+static int device_sms() {
+    static std::mutex mu;
+    static std::unordered_map<int, int> cache;
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 152;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+        (void)cudaGetLastError();
+        n = 152;
+    }
+    cache.emplace(dev, n);
+    return n;
+}
+
+// Tile-planes per adjoint unit for one volume by a cost model of the partials
+// kernel plus the reduce.  Units run in rounds over the launch's warp slots
+// (SMs x warps per SM); a last, partial round costs about as long as
+// (0.6 + 0.4 x its fill) of a full one (a lone warp per SM runs faster, not
+// proportionally so).  Per zchunk zc:
+//   T = rounds / (units / slots) * (gradient + partial bytes) * (1 + 0.3 / zc)
+//       + partial bytes (read back by the reduce),
+// 0.3 tile-planes being the start-up and flush cost of a unit.  Measured on
+// the GPU the model ranks the good and bad choices of 512^3 / 512^2 x 300
+// volumes at spacings 3, 5 and 8 correctly to within a few per cent.
+// Only plans of at most max_floats partial floats are considered (when >= 0);
+// if none fits, the smallest plan.
+static int choose_zchunk(const InstDesc& d0, bool tma, long long max_floats = -1) {
+    if (d0.ncz <= 0 || d0.units <= 0) return kDefaultZChunk;
+    int wps = 3 * kAdjWarpsMax;   // row path: three 4-warp CTAs per SM
+    if (tma) {
+        const int blk = tma_block_bytes(d0.dx, d0.tma_rows);
+        wps = tma_warps_per_cta(blk, tma_default_stages(blk), 0);
+    }
+    const double slots = (double)device_sms() * wps;
+    const double grad_bytes = 12.0 * d0.X * d0.Y * d0.Z;
+    InstDesc d = d0;
+    int best = -1, smallest = kDefaultZChunk;
+    double best_t = 0;
+    long long smallest_f = -1;
+    for (int zc = kMinZChunk; zc <= kMaxZChunk; ++zc) {
+        set_zchunk(d, zc);
+        if (smallest_f < 0 || adj_floats(d) < smallest_f) {
+            smallest_f = adj_floats(d);
+            smallest = zc;
+        }
+        if (max_floats >= 0 && adj_floats(d) > max_floats) continue;
+        const double n = (double)d.units / slots;
+        const double full = (double)(long long)n, f = n - full;
+        const double rounds = full + (f > 1e-9 ? 0.6 + 0.4 * f : 0.0);
+        const double part_bytes = 4.0 * (double)adj_floats(d);
+        const double t = rounds / n * (grad_bytes + part_bytes) * (1.0 + 0.3 / zc) + part_bytes;
+        if (best < 0 || t < best_t) {
+            best = zc;
+            best_t = t;
+        }
+    }
+    return best < 0 ? smallest : best;
 }
 
 // A launch group: up to kMaxBatch instances that share a kernel variant.
@@ -328,14 +419,22 @@ static bsi_status check_instances(const bsi_instance* inst, int n, bool fwd, boo
     return BSI_OK;
 }
 
-static std::vector<InstDesc> descs(const bsi_instance* inst, int n, bool adjoint, bool bf16 = false) {
+// Instance descriptors; for the adjoint (with the tensor-copy path allowed or
+// not, as the launch will run) zchunk comes from choose_zchunk unless the
+// tile-config table fixes it.
+static std::vector<InstDesc> descs(const bsi_instance* inst, int n, bool adjoint, bool bf16 = false,
+                                   bool allow_tma = false, long long max_floats = -1) {
     std::vector<InstDesc> v((size_t)n);
     for (int i = 0; i < n; ++i) {
-        fill_desc(v[(size_t)i], inst[i].geom, adjoint, bf16);
-        v[(size_t)i].phi = inst[i].phi;
-        v[(size_t)i].field = inst[i].field;
-        v[(size_t)i].grad = inst[i].grad_field;
-        v[(size_t)i].dphi = inst[i].grad_phi;
+        InstDesc& d = v[(size_t)i];
+        fill_desc(d, inst[i].geom, adjoint, bf16);
+        d.phi = inst[i].phi;
+        d.field = inst[i].field;
+        d.grad = inst[i].grad_field;
+        d.dphi = inst[i].grad_phi;
+        const bsi_geom& g = inst[i].geom;
+        if (adjoint && lookup_config(g.dx, g.dy, g.dz).adj_zchunk == 0)
+            set_zchunk(d, choose_zchunk(d, allow_tma && tma_geometry_ok(d), max_floats));
     }
     return v;
 }
@@ -353,12 +452,22 @@ static bsi_status forward_impl(const bsi_instance* inst, int n, bsi_dtype dt, cu
     return BSI_OK;
 }
 
-static bsi_status adjoint_impl(const bsi_instance* inst, int n, void* ws, size_t ws_bytes, cudaStream_t s) {
+// fixed_scratch: ws is the library's no-alloc array; plans are chosen to fit
+// it, and only the chosen plan's size is checked.
+static bsi_status adjoint_impl(const bsi_instance* inst, int n, void* ws, size_t ws_bytes, cudaStream_t s,
+                               bool fixed_scratch = false) {
     bsi_status st = check_instances(inst, n, false, true, BSI_F32);
     if (st != BSI_OK) return st;
     long long ws_floats = 0;
-    const std::vector<Group> groups = plan(descs(inst, n, true), &ws_floats, tensor_map_encoder() != nullptr);
-    if ((size_t)ws_floats * sizeof(float) > ws_bytes) return BSI_ERR_WORKSPACE;
+    const bool tma = tensor_map_encoder() != nullptr;
+    const std::vector<Group> groups =
+        plan(descs(inst, n, true, false, tma, fixed_scratch ? (long long)(ws_bytes / sizeof(float)) : -1),
+             &ws_floats, tma);
+    // the documented size (the bound over zchunk choices), not only this plan's
+    long long bound = 0;
+    if (!fixed_scratch)
+        for (int i = 0; i < n; ++i) bound += adj_floats_bound(inst[i].geom);
+    if ((size_t)std::max(bound, ws_floats) * sizeof(float) > ws_bytes) return BSI_ERR_WORKSPACE;
     if (ws_floats > 0 && !ws) return BSI_ERR_WORKSPACE;
     if (ws && misaligned(ws, 16)) return BSI_ERR_ALIGN;
     float* part = static_cast<float*>(ws);
@@ -608,9 +717,7 @@ bsi_status bsi_field_forward(const bsi_geom* g, const float* phi, void* field, b
 
 size_t bsi_adjoint_workspace_bytes(const bsi_geom* g) {
     if (check_geom(g) != BSI_OK) return 0;
-    InstDesc d;
-    fill_desc(d, *g, true);
-    return (size_t)adj_floats(d) * sizeof(float);
+    return (size_t)adj_floats_bound(*g) * sizeof(float);
 }
 
 bsi_status bsi_field_adjoint(const bsi_geom* g, const float* grad_field, float* grad_phi, void* workspace,
@@ -633,9 +740,7 @@ size_t bsi_batched_adjoint_workspace_bytes(const bsi_instance* inst, int n) {
     long long total = 0;
     for (int i = 0; i < n; ++i) {
         if (check_geom(&inst[i].geom) != BSI_OK) return 0;
-        InstDesc d;
-        fill_desc(d, inst[i].geom, true);
-        total += adj_floats(d);
+        total += adj_floats_bound(inst[i].geom);
     }
     return (size_t)total * sizeof(float);
 }
@@ -682,7 +787,6 @@ bsi_status bsi_get_tile_config(int32_t dx, int32_t dy, int32_t dz, bsi_tile_conf
     c.dx = dx;
     c.dy = dy;
     c.dz = dz;
-    if (c.adj_zchunk == 0) c.adj_zchunk = kDefaultZChunk;
     if (c.adj_warps == 0) c.adj_warps = kAdjWarpsMax;
     if (c.fwd_warps == 0) c.fwd_warps = kMaxWarpsPerCta;
     // fwd_strip_tiles stays 0 when unset: it then depends on the volume (X % 4) and dtype
@@ -731,7 +835,7 @@ int bsi_selfcheck_ranges(const bsi_instance* inst, int n, int op, int cover, cha
             }
         } else {
             long long ws = 0;
-            const std::vector<Group> groups = plan(descs(inst, n, true), &ws, true);
+            const std::vector<Group> groups = plan(descs(inst, n, true, false, true), &ws, true);
             for (const Group& g : groups) {
                 check_adjoint_group(g, ws, rc, cover != 0);
                 long long total = 0;
@@ -796,12 +900,13 @@ extern "C" bsi_status bsi_field_adjoint_noalloc(const bsi_geom* g, const float* 
     in.grad_phi = grad_phi;
     const bsi_status st = check_instances(&in, 1, false, true, BSI_F32);
     if (st != BSI_OK) return st;
-    const size_t need = bsi_adjoint_workspace_bytes(g);
+    // the smallest plan must fit; adjoint_impl then picks among the plans that do
+    const size_t need = empty_volume(*g) ? 0 : (size_t)adj_floats_bound(*g, true) * sizeof(float);
     if (need > kNoAllocScratchBytes) return BSI_ERR_SCRATCH_LIMIT;
     void* scratch = nullptr;
     if (need > 0) {
         const cudaError_t e = noalloc_scratch(&scratch);
         if (e != cudaSuccess) return cuda_fail(e);
     }
-    return adjoint_impl(&in, 1, scratch, kNoAllocScratchBytes, reinterpret_cast<cudaStream_t>(stream));
+    return adjoint_impl(&in, 1, scratch, kNoAllocScratchBytes, reinterpret_cast<cudaStream_t>(stream), true);
 }

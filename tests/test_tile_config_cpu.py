@@ -19,7 +19,7 @@ def clean_table():
 
 def test_defaults_and_lookup():
     d = B.bsi_get_tile_config((5, 5, 5))
-    assert d == {"dx": 5, "dy": 5, "dz": 5, "adj_zchunk": 4, "adj_warps": 4, "fwd_strip_tiles": 0, "fwd_warps": 8}
+    assert d == {"dx": 5, "dy": 5, "dz": 5, "adj_zchunk": 0, "adj_warps": 4, "fwd_strip_tiles": 0, "fwd_warps": 8}
     B.bsi_set_tile_configs([{"dx": 5, "dy": 5, "dz": 5, "adj_zchunk": 6},
                             {"dx": 3, "adj_zchunk": 8, "fwd_strip_tiles": 16},
                             {"adj_warps": 2}])
