@@ -315,6 +315,15 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
     res = {}
     iters = 50
 
+    # write-only HBM denominator: the library's own 2 GiB fill through the
+    # forward's store path (bsi_probe_fill), best of 10
+    buf = torch.empty(2 << 30, dtype=torch.uint8, device=dev)
+    wbest = min(time_fn(lambda: P.bsi_probe_fill(buf, 7), s, 3, warm=1) for _ in range(10))
+    write_peak = buf.numel() / wbest / 1e6
+    del buf
+    res["hbm_write_peak"] = {"gbs": round(write_peak, 1), "how": "bsi_probe_fill of 2 GiB, best of 10 x 3 launches",
+                             "nominal_gbs": 7900.0}
+
     # forward-only FP32 / BF16 and adjoint-only on the CT volume
     ms = time_fn(lambda: P.bsi_field_forward(phi, shape, spacing, out=field), s, iters)
     b16 = torch.empty(shape + (3,), dtype=torch.bfloat16, device=dev)
@@ -322,7 +331,9 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
     msa = time_fn(lambda: P.bsi_field_adjoint(grad, spacing, out=dphi, workspace=work), s, iters)
     res["components"] = {
         "fwd_f32": {"gvox_s": round(nvox / ms / 1e6, 2), "ms": round(ms, 5),
-                    "gbs": round(model.forward_bytes(shape, spacing) / ms / 1e6, 1)},
+                    "gbs": round(model.forward_bytes(shape, spacing) / ms / 1e6, 1),
+                    "frac_of_write_peak": round(model.forward_bytes(shape, spacing) / ms / 1e6 / write_peak, 4),
+                    "frac_of_nominal": round(model.forward_bytes(shape, spacing) / ms / 1e6 / 7900.0, 4)},
         "fwd_bf16": {"gvox_s": round(nvox / ms16 / 1e6, 2), "ms": round(ms16, 5),
                      "gbs": round(model.forward_bytes(shape, spacing, 2) / ms16 / 1e6, 1)},
         "adjoint": {"gvox_s": round(nvox / msa / 1e6, 2), "ms": round(msa, 5),
@@ -343,6 +354,21 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
             "frac_of_hbm": round(gbs / hbm_peak, 4)}
     res["sweep_512cubed_fwd"] = sweep
     del out
+
+    # 512^3 spacing sweep (adjoint)
+    sweep = {}
+    g = torch.randn(big + (3,), device=dev)
+    for sp in [(3, 3, 3), (5, 5, 5), (6, 5, 4), (8, 8, 8)]:
+        d_ = torch.empty(synth.grid_shape(big, sp) + (3,), device=dev)
+        w_ = torch.empty(P.bsi_adjoint_workspace_bytes(big, sp), dtype=torch.uint8, device=dev)
+        t = time_fn(lambda: P.bsi_field_adjoint(g, sp, out=d_, workspace=w_), s, 20)
+        gbs = model.adjoint_bytes(big, sp) / t / 1e6
+        sweep["x".join(str(v) for v in sp[::-1])] = {
+            "gvox_s": round(512 ** 3 / t / 1e6, 2), "ms": round(t, 5), "gbs": round(gbs, 1),
+            "frac_of_hbm": round(gbs / hbm_peak, 4)}
+        del d_, w_
+    res["sweep_512cubed_adj"] = sweep
+    del g
 
     # 64-volume uneven batch, forward + adjoint, replayed as one CUDA graph
     geoms = synth.batch_geometries(64, seed=5)

@@ -217,6 +217,16 @@ bsi_status bsi_check_device_status(bsi_stream_t stream, uint32_t* flags);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int bsi_version(void);
 
+/* Measurement utility, no counterpart in the paper: fills `bytes` bytes at
+ * device address dst with the 32-bit pattern `value`, through the forward
+ * kernel's store path (TMA bulk copies from shared memory, 16 KB each, from
+ * every SM), so that its time gives the write-only HBM peak, the denominator
+ * of the forward's store roofline.  dst and bytes must be multiples of 16
+ * (BSI_ERR_ALIGN); dst NULL with bytes > 0 is BSI_ERR_NULL; bytes == 0 does
+ * nothing.  Enqueued on `stream`, allocates nothing; BSI_ERR_CUDA if the launch
+ * fails. */
+bsi_status bsi_probe_fill(void* dst, size_t bytes, uint32_t value, bsi_stream_t stream);
+
 /* Host-only diagnostic, no CUDA call: plans the launches of a batched call of
  * kind op (0 forward FP32, 1 forward BF16, 2 adjoint) exactly as the entry
  * points do, and checks with the kernels' own index functions that every

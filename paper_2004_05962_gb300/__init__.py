@@ -16,6 +16,7 @@ from .bsi import (  # noqa: F401
     bsi_field_forward_batched,
     bsi_field_adjoint_noalloc,
     bsi_get_tile_config,
+    bsi_probe_fill,
     bsi_selfcheck_ranges,
     bsi_set_tile_configs,
     bsi_tile_configs,

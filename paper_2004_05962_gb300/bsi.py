@@ -110,6 +110,7 @@ def library(checked: bool | None = None) -> ctypes.CDLL:
         "bsi_set_tile_configs": (i32, [ctypes.POINTER(BsiTileConfig), i32]),
         "bsi_get_tile_config": (i32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.POINTER(BsiTileConfig)]),
+        "bsi_probe_fill": (i32, [vp, sz, ctypes.c_uint32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -124,7 +125,7 @@ def exported_symbols():
             "bsi_field_forward_batched", "bsi_batched_adjoint_workspace_bytes",
             "bsi_field_adjoint_batched", "bsi_status_string", "bsi_last_cuda_error",
             "bsi_check_device_status", "bsi_version", "bsi_selfcheck_ranges",
-            "bsi_field_adjoint_noalloc", "bsi_set_tile_configs", "bsi_get_tile_config"]
+            "bsi_field_adjoint_noalloc", "bsi_set_tile_configs", "bsi_get_tile_config", "bsi_probe_fill"]
 
 
 def bsi_set_tile_configs(configs) -> None:
@@ -333,6 +334,17 @@ def bsi_field_adjoint_batched(grads, spacings, outs=None, workspace=None, stream
                                              _stream(stream, dev))
     _check(st, "bsi_field_adjoint_batched")
     return outs
+
+
+def bsi_probe_fill(buf: torch.Tensor, value: int = 0, stream=None) -> None:
+    """Fills a contiguous device tensor (size and address multiples of 16 bytes)
+    with a 32-bit pattern through the forward kernel's store path: the
+    write-only HBM peak probe."""
+    if not buf.is_cuda or not buf.is_contiguous():
+        raise BsiError("bsi_probe_fill wants a contiguous CUDA tensor")
+    st = library().bsi_probe_fill(buf.data_ptr(), buf.numel() * buf.element_size(), value & 0xFFFFFFFF,
+                                  _stream(stream, buf.device))
+    _check(st, "bsi_probe_fill")
 
 
 def bsi_check_device_status(stream=None, device=None) -> int:

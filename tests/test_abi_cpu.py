@@ -193,3 +193,11 @@ def test_selfcheck_detects_a_bad_plan(lib):
     arr[0].geom = g
     buf = ctypes.create_string_buffer(256)
     assert lib.bsi_selfcheck_ranges(arr, 1, 0, 1, buf, 256) > 0
+
+
+def test_probe_fill_validation_before_cuda(lib):
+    fake = 0x7F0000000000  # never dereferenced: validation fails first
+    assert lib.bsi_probe_fill(None, 0, 0, None) == 0
+    assert lib.bsi_probe_fill(None, 16, 0, None) == 1
+    assert lib.bsi_probe_fill(fake + 4, 16, 0, None) == 6
+    assert lib.bsi_probe_fill(fake, 20, 0, None) == 6

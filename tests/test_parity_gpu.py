@@ -204,3 +204,15 @@ def test_batched_more_than_one_launch_group():
     for i, (s, d) in enumerate(geoms):
         err, tol = fwd_err(outs[i], phis[i], s, d)
         assert err <= tol, (i, s, d)
+
+
+def test_probe_fill_writes_the_pattern_exactly():
+    """bsi_probe_fill (the write-peak probe): every byte of [dst, dst + bytes)
+    holds the pattern and nothing after it is touched, for whole 16 KB chunks
+    plus a tail."""
+    for nbytes in (16, 16 * 1024, 5 * 16 * 1024 + 48, 3 << 20):
+        buf = torch.zeros(nbytes // 4 + 8, dtype=torch.int32, device=dev())
+        P.bsi_probe_fill(buf[: nbytes // 4], 0x01020304)
+        torch.cuda.synchronize()
+        assert bool((buf[: nbytes // 4] == 0x01020304).all()), nbytes
+        assert bool((buf[nbytes // 4:] == 0).all()), nbytes
