@@ -54,8 +54,10 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.bsi_oracle_forward_points.argtypes = geom + [vp, i32, vp, i64, vp, i32]
     lib.bsi_oracle_adjoint.argtypes = geom + [vp, i32, vp, i32]
     lib.bsi_oracle_adjoint_points.argtypes = geom + [vp, i32, vp, i64, vp, i32]
+    lib.bsi_oracle_resample.argtypes = geom + [vp, i32, vp, i32, i64, i64, i64, vp, i32]
+    lib.bsi_oracle_resample_grad.argtypes = geom + [vp, i32, vp, i32, i64, i64, i64, vp, i32, vp, i32]
     for f in ("bsi_oracle_forward", "bsi_oracle_forward_points", "bsi_oracle_adjoint",
-              "bsi_oracle_adjoint_points"):
+              "bsi_oracle_adjoint_points", "bsi_oracle_resample", "bsi_oracle_resample_grad"):
         getattr(lib, f).restype = i32
     return lib
 
@@ -154,6 +156,46 @@ def adjoint_points(grad, spacing, gxyz, nthreads: int = 0, lib=None) -> np.ndarr
     if rc:
         raise OracleError("bsi_oracle_adjoint_points: bad arguments")
     return out
+
+
+def resample(phi, shape, spacing, image, nthreads: int = 0, lib=None) -> np.ndarray:
+    """Floating ``image`` [fZ, fY, fX] sampled at x + T(x) (trilinear, zeros
+    outside the image): warped [Z, Y, X] (FP64)."""
+    lib = lib or load()
+    Z, Y, X = (int(s) for s in shape)
+    assert phi.shape == grid_shape(shape, spacing) + (3,)
+    p, f32 = _in(phi)
+    im, if32 = _in(image)
+    fZ, fY, fX = im.shape
+    out = np.empty((Z, Y, X), np.float64)
+    rc = lib.bsi_oracle_resample(*_geom(shape, spacing), p.ctypes.data, f32, im.ctypes.data, if32, fX, fY, fZ,
+                                 out.ctypes.data, nthreads)
+    if rc:
+        raise OracleError("bsi_oracle_resample: bad arguments")
+    return out
+
+
+def resample_grad(phi, shape, spacing, image, dwarped, nthreads: int = 0, lib=None) -> np.ndarray:
+    """Voxel gradient G [Z, Y, X, 3] = dwarped * grad F~(x + T(x)) (FP64)."""
+    lib = lib or load()
+    Z, Y, X = (int(s) for s in shape)
+    assert phi.shape == grid_shape(shape, spacing) + (3,) and tuple(dwarped.shape) == (Z, Y, X)
+    p, f32 = _in(phi)
+    im, if32 = _in(image)
+    dw, df32 = _in(dwarped)
+    fZ, fY, fX = im.shape
+    out = np.empty((Z, Y, X, 3), np.float64)
+    rc = lib.bsi_oracle_resample_grad(*_geom(shape, spacing), p.ctypes.data, f32, im.ctypes.data, if32, fX, fY,
+                                      fZ, dw.ctypes.data, df32, out.ctypes.data, nthreads)
+    if rc:
+        raise OracleError("bsi_oracle_resample_grad: bad arguments")
+    return out
+
+
+def resample_backward(phi, shape, spacing, image, dwarped, nthreads: int = 0, lib=None) -> np.ndarray:
+    """dL/dphi [nz, ny, nx, 3] for dL/dwarped = ``dwarped``: the transpose of
+    Eq. 1 applied to resample_grad."""
+    return adjoint(resample_grad(phi, shape, spacing, image, dwarped, nthreads, lib), spacing, nthreads, lib)
 
 
 def threads(nthreads: int = 0, lib=None) -> int:

@@ -397,3 +397,126 @@ int bsi_oracle_adjoint_points(int64_t X, int64_t Y, int64_t Z, int dx, int dy, i
     oracle_parallel(npts, bsi_oracle_threads(nthreads), adj_pts, &c);
     return c.bad ? -1 : 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Resampling of a floating image by the BSI displacement field.              */
+/*                                                                             */
+/* The step of FFD that follows BSI, which the paper proposes to merge with    */
+/* it (Sec. 7): the floating image F [fZ][fY][fX] is sampled at p = x + T(x),  */
+/* T from Eq. 1 at voxel x, in voxel units.  F~ below is the trilinear         */
+/* interpolant of F extended by zeros outside it: with i = floor(p_x),         */
+/* a = p_x - i (likewise j, b and k, c),                                       */
+/*   F~(p) = sum over s, t, r in {0, 1} of                                     */
+/*           (s ? a : 1 - a) (t ? b : 1 - b) (r ? c : 1 - c) F(i+s, j+t, k+r),  */
+/* F taken as 0 at indices outside the image.  Its gradient is the derivative  */
+/* of that sum in a, b and c (one-sided from above at integer positions,       */
+/* where floor() puts them).                                                   */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    const void* F;
+    int in_f32;
+    int64_t fX, fY, fZ;
+} oracle_image;
+
+static double oracle_tap(const oracle_image* im, int64_t i, int64_t j, int64_t k) {
+#if ORACLE_MUTANT == 11 /* edge values repeated outside the image instead of zeros */
+    i = i < 0 ? 0 : (i >= im->fX ? im->fX - 1 : i);
+    j = j < 0 ? 0 : (j >= im->fY ? im->fY - 1 : j);
+    k = k < 0 ? 0 : (k >= im->fZ ? im->fZ - 1 : k);
+#endif
+    if (i < 0 || j < 0 || k < 0 || i >= im->fX || j >= im->fY || k >= im->fZ) return 0.0;
+    return oracle_load(im->F, im->in_f32, (k * im->fY + j) * im->fX + i);
+}
+
+/* F~(p) and, when grad is not NULL, its gradient (d/dp_x, d/dp_y, d/dp_z). */
+static double oracle_trilinear(const oracle_image* im, double px, double py, double pz,
+                               double* grad) {
+    const double fi = floor(px), fj = floor(py), fk = floor(pz);
+    const double a = px - fi, b = py - fj, c = pz - fk;
+    const int64_t i = (int64_t)fi, j = (int64_t)fj, k = (int64_t)fk;
+    double v = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+    for (int s = 0; s < 2; ++s)
+        for (int t = 0; t < 2; ++t)
+            for (int r = 0; r < 2; ++r) {
+                const double f = oracle_tap(im, i + s, j + t, k + r);
+#if ORACLE_MUTANT == 9 /* x weights of the two taps exchanged */
+                const double wx = s ? 1.0 - a : a;
+#else
+                const double wx = s ? a : 1.0 - a;
+#endif
+                const double wy = t ? b : 1.0 - b, wz = r ? c : 1.0 - c;
+                v += wx * wy * wz * f;
+                gx += (s ? 1.0 : -1.0) * wy * wz * f;
+                gy += wx * (t ? 1.0 : -1.0) * wz * f;
+#if ORACLE_MUTANT == 10 /* sign of the z derivative flipped */
+                gz -= wx * wy * (r ? 1.0 : -1.0) * f;
+#else
+                gz += wx * wy * (r ? 1.0 : -1.0) * f;
+#endif
+            }
+    if (grad) {
+        grad[0] = gx;
+        grad[1] = gy;
+        grad[2] = gz;
+    }
+    return v;
+}
+
+typedef struct {
+    const oracle_geom* g;
+    const void* phi;
+    int in_f32;
+    oracle_image im;
+    const void* dW;     /* gradient mode: dL/dwarped [Z][Y][X], else NULL */
+    int dw_f32;
+    double* out;        /* warped [Z][Y][X], or G [Z][Y][X][3] in gradient mode */
+} rs_ctx;
+
+static void rs_rows(void* c, int64_t b, int64_t e, int tid) {
+    (void)tid;
+    rs_ctx* r = (rs_ctx*)c;
+    const oracle_geom* g = r->g;
+    for (int64_t row = b; row < e; ++row) { /* row = z*Y + y */
+        const int64_t z = row / g->Y, y = row % g->Y;
+        for (int64_t x = 0; x < g->X; ++x) {
+            double T[3], grad[3];
+            oracle_eval(g, r->phi, r->in_f32, x, y, z, T);
+            const int64_t v = row * g->X + x;
+            if (!r->dW) {
+                r->out[v] = oracle_trilinear(&r->im, (double)x + T[0], (double)y + T[1],
+                                             (double)z + T[2], NULL);
+            } else {
+                (void)oracle_trilinear(&r->im, (double)x + T[0], (double)y + T[1], (double)z + T[2],
+                                       grad);
+                const double w = oracle_load(r->dW, r->dw_f32, v);
+                for (int ch = 0; ch < 3; ++ch) r->out[3 * v + ch] = w * grad[ch];
+            }
+        }
+    }
+}
+
+int bsi_oracle_resample(int64_t X, int64_t Y, int64_t Z, int dx, int dy, int dz, const void* phi,
+                        int in_f32, const void* F, int f_f32, int64_t fX, int64_t fY, int64_t fZ,
+                        double* warped, int nthreads) {
+    oracle_geom g;
+    if (oracle_make_geom(&g, X, Y, Z, dx, dy, dz)) return -1;
+    if (fX < 0 || fY < 0 || fZ < 0 || !phi || (X * Y * Z > 0 && !warped) || (fX * fY * fZ > 0 && !F))
+        return -1;
+    rs_ctx c = {&g, phi, in_f32, {F, f_f32, fX, fY, fZ}, NULL, 0, warped};
+    oracle_parallel(Y * Z, bsi_oracle_threads(nthreads), rs_rows, &c);
+    return 0;
+}
+
+int bsi_oracle_resample_grad(int64_t X, int64_t Y, int64_t Z, int dx, int dy, int dz,
+                             const void* phi, int in_f32, const void* F, int f_f32, int64_t fX,
+                             int64_t fY, int64_t fZ, const void* dW, int dw_f32, double* G,
+                             int nthreads) {
+    oracle_geom g;
+    if (oracle_make_geom(&g, X, Y, Z, dx, dy, dz)) return -1;
+    if (fX < 0 || fY < 0 || fZ < 0 || !phi || (X * Y * Z > 0 && (!G || !dW)) ||
+        (fX * fY * fZ > 0 && !F))
+        return -1;
+    rs_ctx c = {&g, phi, in_f32, {F, f_f32, fX, fY, fZ}, dW, dw_f32, G};
+    oracle_parallel(Y * Z, bsi_oracle_threads(nthreads), rs_rows, &c);
+    return 0;
+}

@@ -61,6 +61,24 @@ int bsi_oracle_adjoint_points(int64_t X, int64_t Y, int64_t Z, int dx, int dy, i
                               const void* grad, int in_f32, const int64_t* gxyz,
                               int64_t npts, double* out, int nthreads);
 
+/* Resampling of a floating image F [fZ][fY][fX] by the Eq. 1 displacement
+ * (the FFD step that follows BSI; Sec. 7 proposes merging it with BSI):
+ *   warped[z][y][x] = F~(x + T_x, y + T_y, z + T_z),
+ * F~ the trilinear interpolant of F extended by zeros outside the image, in
+ * voxel units. */
+int bsi_oracle_resample(int64_t X, int64_t Y, int64_t Z, int dx, int dy, int dz,
+                        const void* phi, int in_f32, const void* F, int f_f32,
+                        int64_t fX, int64_t fY, int64_t fZ, double* warped, int nthreads);
+
+/* Voxel gradient of a loss L(warped) through the resampling:
+ *   G[z][y][x][c] = dW[z][y][x] * dF~/dp_c (x + T(x)),  dW = dL/dwarped,
+ * the derivative of the trilinear sum, one-sided from above at integer
+ * positions.  dL/dphi is then the adjoint (transpose of Eq. 1) of G. */
+int bsi_oracle_resample_grad(int64_t X, int64_t Y, int64_t Z, int dx, int dy, int dz,
+                             const void* phi, int in_f32, const void* F, int f_f32,
+                             int64_t fX, int64_t fY, int64_t fZ, const void* dW, int dw_f32,
+                             double* G, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif

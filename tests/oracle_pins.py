@@ -291,6 +291,148 @@ def pin_points_match_dense(lib):
     return worst, 1e-12
 
 
+# ---------------------------------------------------------------- resampling
+# The floating image sampled at x + T(x), trilinear with zeros outside (the FFD
+# step after BSI that Sec. 7 proposes to merge with it), and its gradient.
+
+RESAMPLE_CASES = [  # (shape, spacing, floating image shape): equal and unequal image sizes
+    ((7, 9, 11), (2, 3, 4), (7, 9, 11)),
+    ((6, 8, 10), (3, 2, 2), (9, 5, 13)),
+]
+
+
+def _grid_points(shape):
+    Z, Y, X = shape
+    return np.meshgrid(np.arange(Z), np.arange(Y), np.arange(X), indexing="ij")
+
+
+def pin_resample_identity(lib):
+    """phi = 0: every sample lands on its own voxel, W = F exactly."""
+    rng = _rng(31)
+    worst = 0.0
+    for shape, spacing, _ in RESAMPLE_CASES:
+        F = rng.normal(size=shape)
+        phi = np.zeros(oracle.grid_shape(shape, spacing) + (3,))
+        worst = max(worst, float(np.max(np.abs(oracle.resample(phi, shape, spacing, F, lib=lib) - F))))
+    return worst, 1e-15
+
+
+def pin_resample_integer_shift(lib):
+    """phi = integer constant (a, b, c): W(x) = F(x + a, y + b, z + c), and 0 where
+    that voxel lies outside the floating image (of another size than the volume)."""
+    rng = _rng(32)
+    worst = 0.0
+    for shape, spacing, fshape in RESAMPLE_CASES:
+        F = rng.normal(size=fshape)
+        for shift in [(2, -1, 3), (-3, 2, -1), (0, 4, 0)]:
+            phi = np.broadcast_to(np.array(shift, np.float64), oracle.grid_shape(shape, spacing) + (3,)).copy()
+            W = oracle.resample(phi, shape, spacing, F, lib=lib)
+            z, y, x = _grid_points(shape)
+            xs, ys, zs = x + shift[0], y + shift[1], z + shift[2]
+            fZ, fY, fX = fshape
+            inside = (xs >= 0) & (xs < fX) & (ys >= 0) & (ys < fY) & (zs >= 0) & (zs < fZ)
+            want = np.where(inside, F[np.clip(zs, 0, fZ - 1), np.clip(ys, 0, fY - 1), np.clip(xs, 0, fX - 1)], 0.0)
+            worst = max(worst, float(np.max(np.abs(W - want))))
+    return worst, 1e-12
+
+
+def _scipy_sample(F, px, py, pz):
+    """scipy's order-1 spline interpolation with zeros beyond the edges (a library
+    routine for the trilinear interpolant extended by zeros)."""
+    from scipy import ndimage
+
+    return ndimage.map_coordinates(F, [pz.ravel(), py.ravel(), px.ravel()], order=1, mode="grid-constant",
+                                   cval=0.0).reshape(px.shape)
+
+
+def pin_resample_scipy(lib):
+    """Random displacements of several voxels (many samples fall outside the
+    image): W equals scipy.ndimage.map_coordinates(order=1, mode='grid-constant')
+    at x + T(x), T from the (pinned) forward."""
+    rng = _rng(33)
+    worst, scale = 0.0, 1.0
+    for shape, spacing, fshape in RESAMPLE_CASES:
+        F = rng.normal(size=fshape)
+        phi = rng.uniform(-4, 4, oracle.grid_shape(shape, spacing) + (3,))
+        T = oracle.forward(phi, shape, spacing, lib=lib)
+        z, y, x = _grid_points(shape)
+        want = _scipy_sample(F, x + T[..., 0], y + T[..., 1], z + T[..., 2])
+        W = oracle.resample(phi, shape, spacing, F, lib=lib)
+        worst = max(worst, float(np.max(np.abs(W - want))))
+        scale = max(scale, float(np.max(np.abs(F))))
+    return worst, 1e-12 * scale
+
+
+def pin_resample_affine_image(lib):
+    """F affine in the voxel coordinates and every sample inside the image:
+    trilinear interpolation reproduces it, W(x) = k . (x + T(x)) + c."""
+    rng = _rng(34)
+    worst, scale = 0.0, 1.0
+    shape, spacing = (10, 11, 12), (3, 2, 4)
+    Z, Y, X = shape
+    k, c0 = rng.uniform(-2, 2, 3), 0.7
+    z, y, x = _grid_points(shape)
+    F = k[0] * x + k[1] * y + k[2] * z + c0
+    phi = rng.uniform(-0.9, 0.9, oracle.grid_shape(shape, spacing) + (3,))
+    T = oracle.forward(phi, shape, spacing, lib=lib)
+    p = np.stack([x + T[..., 0], y + T[..., 1], z + T[..., 2]], -1)
+    inside = np.all((p >= 0) & (p <= np.array([X - 1, Y - 1, Z - 1])), axis=-1)
+    W = oracle.resample(phi, shape, spacing, F, lib=lib)
+    want = p @ k + c0
+    worst = float(np.max(np.abs(W - want)[inside]))
+    scale = float(np.max(np.abs(want)))
+    assert inside.mean() > 0.5
+    return worst, 1e-13 * scale
+
+
+def pin_resample_grad_scipy_fd(lib):
+    """G / dW is the gradient of the interpolant at x + T(x): central differences
+    of scipy's interpolant (samples with any coordinate within 1e-3 of an
+    integer, where the interpolant has a kink, are left out)."""
+    rng = _rng(35)
+    worst, scale = 0.0, 1.0
+    for shape, spacing, fshape in RESAMPLE_CASES:
+        F = rng.normal(size=fshape)
+        phi = rng.uniform(-3, 3, oracle.grid_shape(shape, spacing) + (3,))
+        dW = rng.normal(size=shape)
+        G = oracle.resample_grad(phi, shape, spacing, F, dW, lib=lib)
+        T = oracle.forward(phi, shape, spacing, lib=lib)
+        z, y, x = _grid_points(shape)
+        p = [x + T[..., 0], y + T[..., 1], z + T[..., 2]]
+        frac = np.stack([q - np.floor(q) for q in p], -1)
+        ok = np.all((frac > 1e-3) & (frac < 1 - 1e-3), axis=-1)
+        h = 1e-6
+        for ch in range(3):
+            hi = [q + (h if i == ch else 0.0) for i, q in enumerate(p)]
+            lo = [q - (h if i == ch else 0.0) for i, q in enumerate(p)]
+            fd = (_scipy_sample(F, *hi) - _scipy_sample(F, *lo)) / (2 * h)
+            worst = max(worst, float(np.max(np.abs(G[..., ch] - dW * fd)[ok])))
+        scale = max(scale, float(np.max(np.abs(G))))
+    return worst, 1e-7 * scale
+
+
+def pin_resample_backward_fd(lib):
+    """dL/dphi (adjoint of G) against central differences of
+    L(phi) = sum dW * W(phi) through the oracle's own resampling."""
+    rng = _rng(36)
+    shape, spacing, fshape = (8, 7, 9), (3, 2, 3), (9, 8, 10)
+    F = rng.normal(size=fshape)
+    phi = rng.uniform(-2, 2, oracle.grid_shape(shape, spacing) + (3,))
+    dW = rng.normal(size=shape)
+    grad = oracle.resample_backward(phi, shape, spacing, F, dW, lib=lib)
+    worst = 0.0
+    eps = 1e-7
+    for _ in range(12):
+        idx = tuple(int(rng.integers(0, s)) for s in phi.shape)
+        p1, p2 = phi.copy(), phi.copy()
+        p1[idx] += eps
+        p2[idx] -= eps
+        fd = (np.sum(dW * oracle.resample(p1, shape, spacing, F, lib=lib))
+              - np.sum(dW * oracle.resample(p2, shape, spacing, F, lib=lib))) / (2 * eps)
+        worst = max(worst, abs(fd - grad[idx]))
+    return worst, 1e-5 * max(1.0, float(np.max(np.abs(grad))))
+
+
 ALL_PINS = [
     pin_partition_of_unity,
     pin_affine_reproduction,
@@ -302,6 +444,12 @@ ALL_PINS = [
     pin_adjoint_dot_product,
     pin_adjoint_finite_difference,
     pin_points_match_dense,
+    pin_resample_identity,
+    pin_resample_integer_shift,
+    pin_resample_scipy,
+    pin_resample_affine_image,
+    pin_resample_grad_scipy_fd,
+    pin_resample_backward_fd,
 ]
 
 

@@ -14,6 +14,9 @@ MUTANTS = {
     6: "channels crossed",
     7: "adjoint scatters to the mirrored x neighbour",
     8: "adjoint drops the last z term",
+    9: "resampling: x weights of the two taps exchanged",
+    10: "resampling: sign of the z derivative flipped",
+    11: "resampling: edge values repeated outside the image",
 }
 
 
