@@ -217,6 +217,56 @@ bsi_status bsi_check_device_status(bsi_stream_t stream, uint32_t* flags);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int bsi_version(void);
 
+/* ------------------------------------------------------------------------
+ * BSI fused with the resampling of the floating image.
+ *
+ * In FFD registration the dense field of Eq. 1 exists to resample the
+ * floating image (Sec. 6: NiftyReg interpolates the coarse control grid into
+ * the fine deformation field, then warps the floating image with it); the
+ * paper proposes merging such steps with BSI (Sec. 7).  These calls never
+ * store the field: each voxel's displacement T(x) becomes the sample position
+ *   p = x + T(x)   (voxel units; floating-image voxel i sits at coordinate i)
+ * of the floating image F, read with the trilinear interpolant of F extended
+ * by zeros outside it:
+ *   F~(p) = sum over s, t, r in {0, 1} of
+ *           (s ? a : 1 - a) (t ? b : 1 - b) (r ? c : 1 - c) F[k+r][j+t][i+s],
+ *   i = floor(p_x), a = p_x - i (likewise j, b for y and k, c for z),
+ *   F taken as 0 at indices outside [0, fX) x [0, fY) x [0, fZ).
+ * F must be finite (a tap outside the image reads an in-range element with
+ * weight 0).
+ * ------------------------------------------------------------------------ */
+
+/* warped[z][y][x] = F~(x + T_x, y + T_y, z + T_z).
+ *   g        : reference volume (X, Y, Z) and spacing; phi [nz][ny][nx][3] on it
+ *   floating : device, FP32 [fZ][fY][fX], fX, fY, fZ in 1..BSI_MAX_DIM (BSI_ERR_DIMS)
+ *   warped   : device, FP32 [Z][Y][X], fully overwritten
+ * Pointers 4-byte aligned (BSI_ERR_ALIGN), non-NULL (BSI_ERR_NULL; phi and
+ * warped may be NULL for an empty volume).  One launch on `stream`. */
+bsi_status bsi_resample_forward(const bsi_geom* g, const float* phi, const float* floating, int64_t fX,
+                                int64_t fY, int64_t fZ, float* warped, bsi_stream_t stream);
+
+/* Workspace bytes bsi_resample_backward needs: the voxel gradient G (12 B per
+ * voxel, 256-byte aligned) followed by the adjoint's workspace (the bound of
+ * bsi_adjoint_workspace_bytes).  0 for an empty volume. */
+size_t bsi_resample_backward_workspace_bytes(const bsi_geom* g);
+
+/* Gradient of a loss L(warped) with respect to phi, given grad_warped = dL/dwarped:
+ *   G[z][y][x][c] = grad_warped[z][y][x] * dF~/dp_c (x + T(x))   (one-sided from
+ *                   above at integer positions, where floor() puts them)
+ *   grad_phi      = transpose of Eq. 1 applied to G (bsi_field_adjoint's sum)
+ * Two stages: one fused launch (Eq. 1 + the interpolant's gradient) writes G
+ * into the workspace, then the adjoint's two launches.
+ *   grad_warped : device, FP32 [Z][Y][X]
+ *   grad_phi    : device, FP32 [nz][ny][nx][3], fully overwritten
+ *   workspace   : device, >= bsi_resample_backward_workspace_bytes(g) bytes,
+ *                 16-byte aligned; contents on entry ignored
+ * Same argument checks as bsi_resample_forward; BSI_ERR_WORKSPACE for a
+ * missing or short workspace.  The gradient with respect to the floating
+ * image is not computed. */
+bsi_status bsi_resample_backward(const bsi_geom* g, const float* phi, const float* floating, int64_t fX,
+                                 int64_t fY, int64_t fZ, const float* grad_warped, float* grad_phi,
+                                 void* workspace, size_t workspace_bytes, bsi_stream_t stream);
+
 /* Measurement utility, no counterpart in the paper: fills `bytes` bytes at
  * device address dst with the 32-bit pattern `value`, through the forward
  * kernel's store path (TMA bulk copies from shared memory, 16 KB each, from
@@ -228,7 +278,8 @@ int bsi_version(void);
 bsi_status bsi_probe_fill(void* dst, size_t bytes, uint32_t value, bsi_stream_t stream);
 
 /* Host-only diagnostic, no CUDA call: plans the launches of a batched call of
- * kind op (0 forward FP32, 1 forward BF16, 2 adjoint) exactly as the entry
+ * kind op (0 forward FP32, 1 forward BF16, 2 adjoint, 3 / 4 the resampling's
+ * value / gradient launch, on each instance's geometry) exactly as the entry
  * points do, and checks with the kernels' own index functions that every
  * global read and write lies inside its buffer and every staging copy fits
  * its shared-memory buffer.  With cover != 0 it also checks that the forward

@@ -17,10 +17,13 @@ from .bsi import (  # noqa: F401
     bsi_field_adjoint_noalloc,
     bsi_get_tile_config,
     bsi_probe_fill,
+    bsi_resample_backward,
+    bsi_resample_backward_workspace_bytes,
+    bsi_resample_forward,
     bsi_selfcheck_ranges,
     bsi_set_tile_configs,
     bsi_tile_configs,
     grid_shape,
     library,
 )
-from .autograd import BSIField, field  # noqa: F401
+from .autograd import BSIField, BSIResample, field, resample  # noqa: F401

@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import torch
 
-from .bsi import bsi_field_adjoint, bsi_field_forward
+from .bsi import bsi_field_adjoint, bsi_field_forward, bsi_resample_backward, bsi_resample_forward
 
 
 class BSIField(torch.autograd.Function):
@@ -30,3 +30,32 @@ def field(phi: torch.Tensor, shape, spacing) -> torch.Tensor:
     """Dense displacement field [Z, Y, X, 3] from control grid phi [nz, ny, nx, 3]
     (shape = (Z, Y, X), spacing = (dz, dy, dx) voxels), differentiable in phi."""
     return BSIField.apply(phi, tuple(int(s) for s in shape), tuple(int(s) for s in spacing))
+
+
+class BSIResample(torch.autograd.Function):
+    """Floating image resampled by the BSI displacement, without storing the
+    field: forward ``bsi_resample_forward``, backward (with respect to phi only)
+    ``bsi_resample_backward``."""
+
+    @staticmethod
+    def forward(ctx, phi, image, shape, spacing):
+        ctx.shape = tuple(int(s) for s in shape)
+        ctx.spacing = tuple(int(s) for s in spacing)
+        phi, image = phi.contiguous(), image.contiguous()
+        ctx.save_for_backward(phi, image)
+        return bsi_resample_forward(phi, ctx.shape, ctx.spacing, image)
+
+    @staticmethod
+    def backward(ctx, grad_warped):
+        phi, image = ctx.saved_tensors
+        g = grad_warped.contiguous()
+        if g.dtype != torch.float32:
+            g = g.float()
+        return bsi_resample_backward(phi, ctx.shape, ctx.spacing, image, g), None, None, None
+
+
+def resample(phi: torch.Tensor, image: torch.Tensor, shape, spacing) -> torch.Tensor:
+    """Floating ``image`` [fZ, fY, fX] sampled at x + T(x) for every voxel x of a
+    (Z, Y, X) = ``shape`` volume, T the BSI displacement of ``phi`` (trilinear,
+    zeros outside the image); differentiable in phi."""
+    return BSIResample.apply(phi, image, tuple(int(s) for s in shape), tuple(int(s) for s in spacing))

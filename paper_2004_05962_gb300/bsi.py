@@ -111,6 +111,10 @@ def library(checked: bool | None = None) -> ctypes.CDLL:
         "bsi_get_tile_config": (i32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.POINTER(BsiTileConfig)]),
         "bsi_probe_fill": (i32, [vp, sz, ctypes.c_uint32, vp]),
+        "bsi_resample_forward": (i32, [G, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp, vp]),
+        "bsi_resample_backward_workspace_bytes": (sz, [G]),
+        "bsi_resample_backward": (i32, [G, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp, vp, vp,
+                                        sz, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -125,7 +129,8 @@ def exported_symbols():
             "bsi_field_forward_batched", "bsi_batched_adjoint_workspace_bytes",
             "bsi_field_adjoint_batched", "bsi_status_string", "bsi_last_cuda_error",
             "bsi_check_device_status", "bsi_version", "bsi_selfcheck_ranges",
-            "bsi_field_adjoint_noalloc", "bsi_set_tile_configs", "bsi_get_tile_config", "bsi_probe_fill"]
+            "bsi_field_adjoint_noalloc", "bsi_set_tile_configs", "bsi_get_tile_config", "bsi_probe_fill",
+            "bsi_resample_forward", "bsi_resample_backward_workspace_bytes", "bsi_resample_backward"]
 
 
 def bsi_set_tile_configs(configs) -> None:
@@ -336,12 +341,61 @@ def bsi_field_adjoint_batched(grads, spacings, outs=None, workspace=None, stream
     return outs
 
 
+def _floating(image):
+    _need(image, "image", torch.float32, tuple(image.shape))
+    if image.dim() != 3:
+        raise ValueError("the floating image is [fZ, fY, fX]")
+    fZ, fY, fX = (int(v) for v in image.shape)
+    return fX, fY, fZ
+
+
+def bsi_resample_forward(phi, shape, spacing, image, out=None, stream=None):
+    """Floating ``image`` [fZ, fY, fX] sampled at x + T(x) (T: Eq. 1 from ``phi``),
+    trilinear with zeros outside the image: warped [Z, Y, X], without storing T."""
+    shape = tuple(int(s) for s in shape)
+    _need(phi, "phi", torch.float32, grid_shape(shape, spacing) + (3,))
+    fX, fY, fZ = _floating(image)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=phi.device)
+    _need(out, "out", torch.float32, shape)
+    g = make_geom(shape, spacing)
+    st = library().bsi_resample_forward(ctypes.byref(g), phi.data_ptr(), image.data_ptr(), fX, fY, fZ,
+                                        out.data_ptr(), _stream(stream, phi.device))
+    _check(st, "bsi_resample_forward")
+    return out
+
+
+def bsi_resample_backward_workspace_bytes(shape, spacing) -> int:
+    g = make_geom(shape, spacing)
+    return int(library().bsi_resample_backward_workspace_bytes(ctypes.byref(g)))
+
+
+def bsi_resample_backward(phi, shape, spacing, image, grad_warped, out=None, workspace=None, stream=None):
+    """dL/dphi [nz, ny, nx, 3] for dL/dwarped = ``grad_warped`` [Z, Y, X]."""
+    shape = tuple(int(s) for s in shape)
+    _need(phi, "phi", torch.float32, grid_shape(shape, spacing) + (3,))
+    _need(grad_warped, "grad_warped", torch.float32, shape)
+    fX, fY, fZ = _floating(image)
+    if out is None:
+        out = torch.empty_like(phi)
+    _need(out, "out", torch.float32, tuple(phi.shape))
+    g = make_geom(shape, spacing)
+    need = int(library().bsi_resample_backward_workspace_bytes(ctypes.byref(g)))
+    ws, wsb = _workspace(need, phi.device, workspace)
+    st = library().bsi_resample_backward(ctypes.byref(g), phi.data_ptr(), image.data_ptr(), fX, fY, fZ,
+                                         grad_warped.data_ptr(), out.data_ptr(),
+                                         ws.data_ptr() if ws is not None else None, wsb,
+                                         _stream(stream, phi.device))
+    _check(st, "bsi_resample_backward")
+    return out
+
+
 def bsi_probe_fill(buf: torch.Tensor, value: int = 0, stream=None) -> None:
     """Fills a contiguous device tensor (size and address multiples of 16 bytes)
     with a 32-bit pattern through the forward kernel's store path: the
     write-only HBM peak probe."""
     if not buf.is_cuda or not buf.is_contiguous():
-        raise BsiError("bsi_probe_fill wants a contiguous CUDA tensor")
+        raise ValueError("bsi_probe_fill wants a contiguous CUDA tensor")
     st = library().bsi_probe_fill(buf.data_ptr(), buf.numel() * buf.element_size(), value & 0xFFFFFFFF,
                                   _stream(stream, buf.device))
     _check(st, "bsi_probe_fill")
@@ -358,8 +412,9 @@ def bsi_check_device_status(stream=None, device=None) -> int:
 
 def bsi_selfcheck_ranges(shapes, spacings, op: str = "forward", cover: bool = True):
     """Host-only range check of every kernel access for a planned call (no GPU).
-    ``op`` is "forward", "forward_bf16" or "adjoint".  Returns (violations, message)."""
-    code = {"forward": 0, "forward_bf16": 1, "adjoint": 2}[op]
+    ``op`` is "forward", "forward_bf16", "adjoint", "resample" or "resample_grad".
+    Returns (violations, message)."""
+    code = {"forward": 0, "forward_bf16": 1, "adjoint": 2, "resample": 3, "resample_grad": 4}[op]
     arr = _instances([tuple(s) for s in shapes], spacings)
     buf = ctypes.create_string_buffer(256)
     n = library().bsi_selfcheck_ranges(arr, len(shapes), code, int(cover), buf, 256)

@@ -530,11 +530,13 @@ static void check_slots(long long total, RangeChecker& rc) {
 // index functions, that each read and write lies inside its buffer, that each
 // staging copy fits its shared-memory buffer, and (when `cover` is set) that
 // the rows of the units tile the field exactly once.
-static void check_forward_group(const Group& g, int es, RangeChecker& rc, bool cover) {
+// ob: output bytes per voxel (12 / 6 forward FP32 / BF16, 4 / 12 resampling
+// value / gradient mode); outputs are checked as voxel ranges.
+static void check_forward_group(const Group& g, int ob, RangeChecker& rc, bool cover) {
     const int buf = stage_buf_bytes(g.dxmax);
     for (const InstDesc& d : g.inst) {
         const long long phi_elems = 3LL * d.nx * d.ny * d.nz;
-        const long long field_elems = 3LL * d.X * d.Y * d.Z;
+        const long long nvox_all = (long long)d.X * d.Y * d.Z;
         std::vector<unsigned char> hit(cover ? (size_t)d.X * d.Y * d.Z : 0, 0);
         for (long long ul = 0; ul < d.units; ++ul) {
             const FwdUnit u = fwd_unit(d, ul);
@@ -553,15 +555,15 @@ static void check_forward_group(const Group& g, int es, RangeChecker& rc, bool c
             const int y0 = u.jy * d.dy, yn = imin(d.dy, d.Y - y0);
             // a specialised spacing stages all 32 lanes x dx voxels (past the row end too)
             const int staged = d.dx <= kMaxSpecializedDx && !g.generic ? kLanes * d.dx : u.nvox;
-            if (u.nvox > staged || 15 + staged * 3 * es > buf) rc.fail("staging overflow", staged, buf);
+            if (u.nvox > staged || 15 + staged * ob > buf) rc.fail("staging overflow", staged, buf);
             if (warps_per_cta(fwd_warp_smem(buf)) * fwd_warp_smem(buf) > kSmemBudget)
                 rc.fail("forward shared memory over budget", buf, kSmemBudget);
             for (int rz = 0; rz < zn; ++rz)
                 for (int ry = 0; ry < yn; ++ry) {
-                    const long long e0 = field_elem(d, z0 + rz, y0 + ry, u.x0);
-                    if (e0 < 0 || e0 + 3LL * u.nvox > field_elems) rc.fail("field write", e0, field_elems);
+                    const long long v0 = field_elem(d, z0 + rz, y0 + ry, u.x0) / 3;   // voxel index
+                    if (v0 < 0 || v0 + u.nvox > nvox_all) rc.fail("field write", v0, nvox_all);
                     if (cover)
-                        for (int x = 0; x < u.nvox; ++x) hit[(size_t)(e0 / 3 + x)]++;
+                        for (int x = 0; x < u.nvox; ++x) hit[(size_t)(v0 + x)]++;
                 }
         }
         if (cover)
@@ -680,6 +682,42 @@ static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecke
     }
 }
 
+// ----------------------------------------------------------- resampling
+
+static bsi_status check_floating(int64_t fX, int64_t fY, int64_t fZ, const float* floating) {
+    if (fX < 1 || fY < 1 || fZ < 1 || fX > BSI_MAX_DIM || fY > BSI_MAX_DIM || fZ > BSI_MAX_DIM) return BSI_ERR_DIMS;
+    if (!floating) return BSI_ERR_NULL;
+    if (misaligned(floating, 4)) return BSI_ERR_ALIGN;
+    return BSI_OK;
+}
+
+// One resampling launch (value or gradient mode) over the forward's units.
+static bsi_status run_resample(const bsi_geom* g, const float* phi, const float* floating, int64_t fX, int64_t fY,
+                               int64_t fZ, const float* grad_warped, void* out, bool grad, cudaStream_t s) {
+    InstDesc d;
+    fill_desc(d, *g, false, false);
+    if (d.units == 0) return BSI_OK;
+    d.phi = phi;
+    d.field = out;
+    d.image = floating;
+    d.gwarp = grad_warped;
+    d.fX = (int)fX;
+    d.fY = (int)fY;
+    d.fZ = (int)fZ;
+    Group grp;
+    grp.generic = d.dx > kMaxSpecializedDx;
+    grp.dxmax = d.dx;
+    grp.warps_req = d.warps_req;
+    grp.inst.push_back(d);
+    Batch<1> b;
+    to_batch(grp, b);
+    (void)cudaGetLastError();
+    const cudaError_t e = launch_resample(b, grad, grp.generic, s, nullptr);
+    return e == cudaSuccess ? BSI_OK : cuda_fail(e);
+}
+
+static size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
+
 }  // namespace bsi
 
 using namespace bsi;
@@ -796,39 +834,84 @@ bsi_status bsi_get_tile_config(int32_t dx, int32_t dy, int32_t dz, bsi_tile_conf
 
 bsi_status bsi_check_device_status(bsi_stream_t stream, uint32_t* flags) {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    static thread_local unsigned words[2];
+    static thread_local unsigned words[3];
     cudaError_t e = forward_err_read_clear(&words[0], s);
     if (e == cudaSuccess) e = adjoint_err_read_clear(&words[1], s);
+    if (e == cudaSuccess) e = resample_err_read_clear(&words[2], s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e);
-    const uint32_t w = words[0] | words[1];
+    const uint32_t w = words[0] | words[1] | words[2];
     if (flags) *flags = w;
     return w ? BSI_ERR_DEVICE_STATUS : BSI_OK;
+}
+
+bsi_status bsi_resample_forward(const bsi_geom* g, const float* phi, const float* floating, int64_t fX, int64_t fY,
+                                int64_t fZ, float* warped, bsi_stream_t stream) {
+    bsi_status st = check_geom(g);
+    if (st != BSI_OK) return st;
+    if ((st = check_floating(fX, fY, fZ, floating)) != BSI_OK) return st;
+    if (empty_volume(*g)) return BSI_OK;
+    if (!phi || !warped) return BSI_ERR_NULL;
+    if (misaligned(phi, 4) || misaligned(warped, 4)) return BSI_ERR_ALIGN;
+    return run_resample(g, phi, floating, fX, fY, fZ, nullptr, warped, false, reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t bsi_resample_backward_workspace_bytes(const bsi_geom* g) {
+    if (check_geom(g) != BSI_OK || empty_volume(*g)) return 0;
+    return round256((size_t)12 * g->X * g->Y * g->Z) + (size_t)adj_floats_bound(*g) * sizeof(float);
+}
+
+bsi_status bsi_resample_backward(const bsi_geom* g, const float* phi, const float* floating, int64_t fX, int64_t fY,
+                                 int64_t fZ, const float* grad_warped, float* grad_phi, void* workspace,
+                                 size_t workspace_bytes, bsi_stream_t stream) {
+    bsi_status st = check_geom(g);
+    if (st != BSI_OK) return st;
+    if ((st = check_floating(fX, fY, fZ, floating)) != BSI_OK) return st;
+    if (!grad_phi) return BSI_ERR_NULL;
+    if (misaligned(grad_phi, 4)) return BSI_ERR_ALIGN;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    bsi_instance in;
+    std::memset(&in, 0, sizeof in);
+    in.geom = *g;
+    in.grad_phi = grad_phi;
+    if (empty_volume(*g)) return adjoint_impl(&in, 1, nullptr, 0, s);   // grad_phi = 0
+    if (!phi || !grad_warped) return BSI_ERR_NULL;
+    if (misaligned(phi, 4) || misaligned(grad_warped, 4)) return BSI_ERR_ALIGN;
+    if (!workspace || workspace_bytes < bsi_resample_backward_workspace_bytes(g)) return BSI_ERR_WORKSPACE;
+    if (misaligned(workspace, 16)) return BSI_ERR_ALIGN;
+    // G = dL/dwarped * grad F~(x + T(x)) into the workspace, then the adjoint of G
+    float* G = static_cast<float*>(workspace);
+    const size_t goff = round256((size_t)12 * g->X * g->Y * g->Z);
+    st = run_resample(g, phi, floating, fX, fY, fZ, grad_warped, G, true, s);
+    if (st != BSI_OK) return st;
+    in.grad_field = G;
+    return adjoint_impl(&in, 1, static_cast<unsigned char*>(workspace) + goff, workspace_bytes - goff, s);
 }
 
 int bsi_version(void) { return 100; }
 
 // Host-only: plans the launches of a batched call exactly as the entry points
 // do and checks every global and shared-memory range the kernels will touch
-// (see RangeChecker).  op: 0 forward F32, 1 forward BF16, 2 adjoint.  With
+// (see RangeChecker).  op: 0 forward F32, 1 forward BF16, 2 adjoint, 3 / 4
+// resampling value / gradient mode (the forward's walk).  With
 // cover != 0 it also checks that forward rows tile each field exactly once and
 // that the reduce reads only partials phase 1 writes (memory ~ field size).
 // Returns the number of violations; the first is described in msg.
 int bsi_selfcheck_ranges(const bsi_instance* inst, int n, int op, int cover, char* msg, size_t msg_len) {
     RangeChecker rc;
-    if (n < 0 || (n > 0 && !inst) || op < 0 || op > 2) {
+    if (n < 0 || (n > 0 && !inst) || op < 0 || op > 4) {
         rc.fail("bad arguments", n, op);
     } else {
         bool ok = true;
         for (int i = 0; i < n; ++i) ok = ok && check_geom(&inst[i].geom) == BSI_OK;
         if (!ok) {
             rc.fail("invalid geometry", n, 0);
-        } else if (op < 2) {
+        } else if (op != 2) {
             std::vector<InstDesc> all = descs(inst, n, false, op == 1);
             all.erase(std::remove_if(all.begin(), all.end(), [](const InstDesc& d) { return d.units == 0; }),
                       all.end());
             for (const Group& g : plan(all, nullptr)) {
-                check_forward_group(g, op == 1 ? 2 : 4, rc, cover != 0);
+                check_forward_group(g, op == 1 ? 6 : op == 3 ? 4 : 12, rc, cover != 0);
                 long long total = 0;
                 for (const InstDesc& d : g.inst) total += d.units;
                 if (cover) check_slots(total, rc);

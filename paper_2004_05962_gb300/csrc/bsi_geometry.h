@@ -52,6 +52,11 @@ struct InstDesc {
     void* field;
     const float* grad;
     float* dphi;
+    // resampling of a floating image by the field (bsi_resample_*)
+    const float* image;     // floating image [fZ][fY][fX]
+    const float* gwarp;     // gradient mode: dL/dwarped [Z][Y][X]
+    int fX, fY, fZ;
+    int rpad;
 };
 
 template <int MAXB>

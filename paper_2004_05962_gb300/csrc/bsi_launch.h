@@ -42,6 +42,12 @@ template <int MAXB>
 cudaError_t launch_adjoint_reduce(const Batch<MAXB>& b, const float* part, long long ws_floats,
                                   cudaStream_t s, LaunchInfo* info);
 
+// BSI fused with the resampling of a floating image (one volume): value mode
+// writes warped [Z][Y][X], gradient mode G [Z][Y][X][3] (d.field), reading
+// dL/dwarped (d.gwarp).
+cudaError_t launch_resample(const Batch<1>& b, bool grad, bool generic, cudaStream_t s, LaunchInfo* info);
+cudaError_t resample_err_read_clear(unsigned* out, cudaStream_t s);
+
 // Reads and clears the kernel error word of each translation unit (enqueued
 // on s; the caller synchronises before looking at *out).
 cudaError_t forward_err_read_clear(unsigned* out, cudaStream_t s);

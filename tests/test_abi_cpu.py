@@ -148,14 +148,14 @@ EDGE_CASES = [
 ]
 
 
-@pytest.mark.parametrize("op", ["forward", "forward_bf16", "adjoint"])
+@pytest.mark.parametrize("op", ["forward", "forward_bf16", "adjoint", "resample", "resample_grad"])
 def test_selfcheck_edge_cases(lib, op):
     for shape, spacing in EDGE_CASES:
         n, msg = P.bsi_selfcheck_ranges([shape], [spacing], op, cover=True)
         assert n == 0, (shape, spacing, msg)
 
 
-@pytest.mark.parametrize("op", ["forward", "adjoint"])
+@pytest.mark.parametrize("op", ["forward", "adjoint", "resample", "resample_grad"])
 def test_selfcheck_random_geometries(lib, op):
     rng = np.random.default_rng(7)
     for _ in range(60):
@@ -201,3 +201,23 @@ def test_probe_fill_validation_before_cuda(lib):
     assert lib.bsi_probe_fill(None, 16, 0, None) == 1
     assert lib.bsi_probe_fill(fake + 4, 16, 0, None) == 6
     assert lib.bsi_probe_fill(fake, 20, 0, None) == 6
+
+
+def test_resample_validation_before_cuda(lib):
+    fake = 0x7F0000000000  # never dereferenced: validation fails first
+    g, _ = _geom(40, 30, 20, 5, 4, 3)
+    rf = lib.bsi_resample_forward
+    assert rf(ctypes.byref(g), fake, fake, 0, 30, 20, fake, None) == 2          # empty floating image
+    assert rf(ctypes.byref(g), fake, None, 40, 30, 20, fake, None) == 1         # floating NULL
+    assert rf(ctypes.byref(g), fake, fake + 2, 40, 30, 20, fake, None) == 6     # floating misaligned
+    assert rf(ctypes.byref(g), None, fake, 40, 30, 20, fake, None) == 1
+    assert rf(ctypes.byref(g), fake, fake, 40, 30, 20, fake + 2, None) == 6
+    need = lib.bsi_resample_backward_workspace_bytes(ctypes.byref(g))
+    assert need >= 12 * 40 * 30 * 20 + lib.bsi_adjoint_workspace_bytes(ctypes.byref(g))
+    rb = lib.bsi_resample_backward
+    assert rb(ctypes.byref(g), fake, fake, 40, 30, 20, fake, fake, fake, need - 16, None) == 7
+    assert rb(ctypes.byref(g), fake, fake, 40, 30, 20, fake, fake, fake + 4, need, None) == 6
+    assert rb(ctypes.byref(g), fake, fake, 40, 30, 20, None, fake, fake, need, None) == 1
+    assert rb(ctypes.byref(g), fake, fake, 40, 30, 20, fake, None, fake, need, None) == 1
+    e, _ = _geom(0, 30, 20, 5, 4, 3)
+    assert lib.bsi_resample_backward_workspace_bytes(ctypes.byref(e)) == 0
