@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="main step only (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle leg")
+    ap.add_argument("--section", choices=["resample"], default=None,
+                    help="run only this extra measurement (profiling runs) and print its JSON")
     return ap.parse_args()
 
 
@@ -306,6 +308,55 @@ def time_fn(fn, s, iters, warm=3):
     return a.elapsed_time(b) / iters
 
 
+def measure_resample(P, synth, model, dev, s, phi, field, dphi, hbm_peak, iters):
+    """BSI fused with the resampling of a floating image on the CT volume: value
+    and gradient with respect to phi; unfused context: our field, then torch's
+    grid_sample."""
+    import numpy as np
+    import torch
+    import torch.nn.functional as TF
+
+    shape, spacing = CT_SHAPE, CT_SPACING
+    nvox = int(np.prod(shape))
+
+    F = torch.zeros(shape, device=dev)
+    Z, Y, X = shape
+    for c, sg, a in synth.blob_params(shape, seed=6):   # separable blobs, evaluated on the device
+        ez = torch.exp(-((torch.arange(Z, device=dev) - c[0]) ** 2) / (2 * sg * sg))
+        ey = torch.exp(-((torch.arange(Y, device=dev) - c[1]) ** 2) / (2 * sg * sg))
+        ex = torch.exp(-((torch.arange(X, device=dev) - c[2]) ** 2) / (2 * sg * sg))
+        F += a * ez[:, None, None] * ey[None, :, None] * ex[None, None, :]
+    Wt = torch.empty(shape, device=dev)
+    ms_rs = time_fn(lambda: P.bsi_resample_forward(phi, shape, spacing, F, out=Wt), s, iters)
+    gW = torch.randn(shape, device=dev)
+    wsr = torch.empty(P.bsi_resample_backward_workspace_bytes(shape, spacing), dtype=torch.uint8, device=dev)
+    ms_rsb = time_fn(lambda: P.bsi_resample_backward(phi, shape, spacing, F, gW, out=dphi, workspace=wsr), s, 20)
+    base = torch.stack(torch.meshgrid(torch.arange(X, device=dev), torch.arange(Y, device=dev),
+                                      torch.arange(Z, device=dev), indexing="xy"), -1).float()
+    base = base.permute(2, 0, 1, 3).contiguous()            # [Z, Y, X, 3] as (x, y, z)
+    norm = torch.tensor([2.0 / (X - 1), 2.0 / (Y - 1), 2.0 / (Z - 1)], device=dev)
+
+    def unfused():
+        P.bsi_field_forward(phi, shape, spacing, out=field)
+        grid = (base + field) * norm - 1.0
+        return TF.grid_sample(F[None, None], grid[None], mode="bilinear", padding_mode="zeros", align_corners=True)
+
+    ms_unf = time_fn(unfused, s, 10)
+    agree = float((unfused()[0, 0] - P.bsi_resample_forward(phi, shape, spacing, F, out=Wt)).abs().max())
+    rb = model.resample_bytes(shape, spacing)
+    rbb = model.resample_backward_bytes(shape, spacing)
+    return {
+        "fwd_ms": round(ms_rs, 5), "fwd_gvox_s": round(nvox / ms_rs / 1e6, 2),
+        "fwd_gbs": round(rb / ms_rs / 1e6, 1), "fwd_frac_of_hbm": round(rb / ms_rs / 1e6 / hbm_peak, 4),
+        "fwd_algorithmic_bytes": rb,
+        "bwd_ms": round(ms_rsb, 5), "bwd_gvox_s": round(nvox / ms_rsb / 1e6, 2),
+        "bwd_gbs_algorithmic": round(rbb / ms_rsb / 1e6, 1),
+        "bwd_bytes_moved": rbb + 24 * nvox,
+        "unfused_field_plus_torch_grid_sample_ms": round(ms_unf, 5),
+        "unfused_max_abs_diff": agree,
+        "image": "sum of 8 Gaussian blobs (sigma 8-20 voxels), seed 6; phi = the bench's CT control grid"}
+
+
 def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_peak):
     import numpy as np
     import torch
@@ -340,6 +391,8 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
                     "gbs": round(model.adjoint_bytes(shape, spacing) / msa / 1e6, 1)},
     }
     del b16
+
+    res["resample"] = measure_resample(P, synth, model, dev, s, phi, field, dphi, hbm_peak, iters)
 
     # 512^3 spacing sweep (forward FP32)
     sweep = {}
@@ -520,6 +573,26 @@ def run_reference(args, ws, rank):
             "gpu_launches": 0}
 
 
+def run_section_resample(args):
+    import torch
+
+    from paper_2004_05962_gb300 import build as pbuild
+
+    pbuild.build()
+    import paper_2004_05962_gb300 as P
+    from paper_2004_05962_gb300 import model, synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    s = torch.cuda.current_stream(dev)
+    phi = torch.from_numpy(synth.gaussian_random_phi(CT_SHAPE, CT_SPACING, 3.0, 2.0, seed=2)).to(dev)
+    field = torch.empty(CT_SHAPE + (3,), device=dev)
+    dphi = torch.empty_like(phi)
+    hbm_peak, _ = measured_peaks()
+    return {"section": "resample", "workload": WORKLOAD,
+            "resample": measure_resample(P, synth, model, dev, s, phi, field, dphi, hbm_peak, args.steps)}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -527,6 +600,9 @@ def main():
         out = run_reference(args, ws, rank)
         if out is not None:
             print(json.dumps(out), flush=True)
+        return
+    if args.section == "resample":
+        print(json.dumps(run_section_resample(args)), flush=True)
         return
     out = run_ours(args, ws, rank, local)
     if rank == 0:

@@ -530,8 +530,8 @@ static void check_slots(long long total, RangeChecker& rc) {
 // index functions, that each read and write lies inside its buffer, that each
 // staging copy fits its shared-memory buffer, and (when `cover` is set) that
 // the rows of the units tile the field exactly once.
-// ob: output bytes per voxel (12 / 6 forward FP32 / BF16, 4 / 12 resampling
-// value / gradient mode); outputs are checked as voxel ranges.
+// ob: staging bytes per voxel (12 / 6 forward FP32 / BF16, 12 for T in both
+// resampling modes); outputs are checked as voxel ranges.
 static void check_forward_group(const Group& g, int ob, RangeChecker& rc, bool cover) {
     const int buf = stage_buf_bytes(g.dxmax);
     for (const InstDesc& d : g.inst) {
@@ -911,7 +911,9 @@ int bsi_selfcheck_ranges(const bsi_instance* inst, int n, int op, int cover, cha
             all.erase(std::remove_if(all.begin(), all.end(), [](const InstDesc& d) { return d.units == 0; }),
                       all.end());
             for (const Group& g : plan(all, nullptr)) {
-                check_forward_group(g, op == 1 ? 6 : op == 3 ? 4 : 12, rc, cover != 0);
+                // staging bytes per voxel: the field (12 FP32, 6 BF16), or T for both
+                // resampling modes (12)
+                check_forward_group(g, op == 1 ? 6 : 12, rc, cover != 0);
                 long long total = 0;
                 for (const InstDesc& d : g.inst) total += d.units;
                 if (cover) check_slots(total, rc);

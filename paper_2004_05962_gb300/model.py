@@ -88,3 +88,19 @@ def adjoint_bytes(shape, spacing):
     """Adjoint: read the FP32 3-channel voxel gradient once, write the grid gradient once."""
     Z, Y, X = shape
     return Z * Y * X * 12 + grid_points(shape, spacing) * 12
+
+
+def resample_bytes(shape, spacing, fshape=None, out_bytes=4):
+    """Algorithmic bytes of the fused BSI + resampling forward: the floating
+    image read once (4 B per element), the warped image written once, the
+    control grid read once.  The displacement field is never stored."""
+    fshape = shape if fshape is None else fshape
+    return 4 * math.prod(fshape) + out_bytes * math.prod(shape) + 12 * grid_points(shape, spacing)
+
+
+def resample_backward_bytes(shape, spacing, fshape=None):
+    """Algorithmic bytes of its gradient with respect to phi: the floating image
+    and dL/dwarped read once, dL/dphi written once (the voxel gradient G that the
+    implementation passes from its first stage to the adjoint is extra)."""
+    fshape = shape if fshape is None else fshape
+    return 4 * math.prod(fshape) + 4 * math.prod(shape) + 12 * grid_points(shape, spacing)

@@ -63,18 +63,31 @@ def normal_field(shape, seed, scale=1.0):
     return out
 
 
-def blob_image(shape, seed, nblobs=8, sigma_range=(8.0, 20.0)):
-    """A smooth FP32 image [Z, Y, X]: a sum of ``nblobs`` isotropic Gaussian blobs
-    with random centres, widths in ``sigma_range`` voxels and amplitudes in [0.5, 1]."""
+def blob_params(shape, seed, nblobs=8, sigma_range=(8.0, 20.0)):
+    """Centres (z, y, x), widths (voxels) and amplitudes of ``nblobs`` Gaussian
+    blobs in a (Z, Y, X) volume: centres ~ U[0, N) per axis, widths ~ U[sigma_range],
+    amplitudes ~ U[0.5, 1]."""
     rng = np.random.default_rng(seed)
     Z, Y, X = (int(s) for s in shape)
-    z, y, x = np.meshgrid(np.arange(Z), np.arange(Y), np.arange(X), indexing="ij")
-    img = np.zeros((Z, Y, X), np.float64)
+    out = []
     for _ in range(nblobs):
         c = rng.uniform([0, 0, 0], [Z, Y, X])
         s = rng.uniform(*sigma_range)
         a = rng.uniform(0.5, 1.0)
-        img += a * np.exp(-((z - c[0]) ** 2 + (y - c[1]) ** 2 + (x - c[2]) ** 2) / (2 * s * s))
+        out.append((c, s, a))
+    return out
+
+
+def blob_image(shape, seed, nblobs=8, sigma_range=(8.0, 20.0)):
+    """A smooth FP32 image [Z, Y, X]: the sum of the blob_params blobs, each the
+    product of three 1-D Gaussians (the isotropic Gaussian, separated)."""
+    Z, Y, X = (int(s) for s in shape)
+    img = np.zeros((Z, Y, X), np.float64)
+    for c, s, a in blob_params(shape, seed, nblobs, sigma_range):
+        ez = np.exp(-((np.arange(Z) - c[0]) ** 2) / (2 * s * s))
+        ey = np.exp(-((np.arange(Y) - c[1]) ** 2) / (2 * s * s))
+        ex = np.exp(-((np.arange(X) - c[2]) ** 2) / (2 * s * s))
+        img += a * ez[:, None, None] * ey[None, :, None] * ex[None, None, :]
     return img.astype(np.float32)
 
 

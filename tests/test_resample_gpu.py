@@ -21,7 +21,8 @@ CASES = [
     ((7, 9, 130), (2, 3, 7), (8, 9, 128), 1.5),        # several x-groups
     ((8, 9, 140), (3, 5, 13), (8, 9, 140), 2.0),       # generic x-spacing
     ((1, 1, 3), (1, 1, 1), (2, 2, 2), 1.0),
-    ((30, 1, 1), (5, 1, 1), (30, 1, 1), 4.0),
+    ((30, 1, 1), (5, 1, 1), (30, 1, 1), 4.0),       # floating image 1 voxel wide and high
+    ((12, 10, 16), (3, 2, 4), (12, 10, 2), 3.0),    # floating image 2 voxels wide
 ]
 
 
