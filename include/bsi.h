@@ -217,6 +217,19 @@ bsi_status bsi_check_device_status(bsi_stream_t stream, uint32_t* flags);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int bsi_version(void);
 
+/* Scalar BSI: Eq. 1 with one channel, for interpolating (zooming) an image
+ * whose samples serve as the control points (Sec. 7 names image
+ * interpolation as another use of the method).  The same kernels as
+ * bsi_field_forward with a channel count of 1:
+ *   out[z][y][x] = sum_{l,m,n} B_l(u) B_m(v) B_n(w) coeff[k+n][j+m][i+l]
+ * with the geometry, border convention and spacing of bsi_field_forward.
+ *   coeff : device, FP32 [nz][ny][nx], read only
+ *   out   : device, [Z][Y][X] of out_dtype (BF16: round to nearest even of the
+ *           FP32 result), fully overwritten
+ * Same argument checks and error codes as bsi_field_forward. */
+bsi_status bsi_scalar_forward(const bsi_geom* g, const float* coeff, void* out, bsi_dtype out_dtype,
+                              bsi_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * BSI fused with the resampling of the floating image.
  *
@@ -279,7 +292,8 @@ bsi_status bsi_probe_fill(void* dst, size_t bytes, uint32_t value, bsi_stream_t 
 
 /* Host-only diagnostic, no CUDA call: plans the launches of a batched call of
  * kind op (0 forward FP32, 1 forward BF16, 2 adjoint, 3 / 4 the resampling's
- * value / gradient launch, on each instance's geometry) exactly as the entry
+ * value / gradient launch, 5 / 6 the scalar forward FP32 / BF16, on each
+ * instance's geometry) exactly as the entry
  * points do, and checks with the kernels' own index functions that every
  * global read and write lies inside its buffer and every staging copy fits
  * its shared-memory buffer.  With cover != 0 it also checks that the forward

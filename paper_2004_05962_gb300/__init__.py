@@ -20,6 +20,7 @@ from .bsi import (  # noqa: F401
     bsi_resample_backward,
     bsi_resample_backward_workspace_bytes,
     bsi_resample_forward,
+    bsi_scalar_forward,
     bsi_selfcheck_ranges,
     bsi_set_tile_configs,
     bsi_tile_configs,

@@ -111,6 +111,7 @@ def library(checked: bool | None = None) -> ctypes.CDLL:
         "bsi_get_tile_config": (i32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.POINTER(BsiTileConfig)]),
         "bsi_probe_fill": (i32, [vp, sz, ctypes.c_uint32, vp]),
+        "bsi_scalar_forward": (i32, [G, vp, vp, i32, vp]),
         "bsi_resample_forward": (i32, [G, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp, vp]),
         "bsi_resample_backward_workspace_bytes": (sz, [G]),
         "bsi_resample_backward": (i32, [G, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp, vp, vp,
@@ -130,7 +131,8 @@ def exported_symbols():
             "bsi_field_adjoint_batched", "bsi_status_string", "bsi_last_cuda_error",
             "bsi_check_device_status", "bsi_version", "bsi_selfcheck_ranges",
             "bsi_field_adjoint_noalloc", "bsi_set_tile_configs", "bsi_get_tile_config", "bsi_probe_fill",
-            "bsi_resample_forward", "bsi_resample_backward_workspace_bytes", "bsi_resample_backward"]
+            "bsi_resample_forward", "bsi_resample_backward_workspace_bytes", "bsi_resample_backward",
+            "bsi_scalar_forward"]
 
 
 def bsi_set_tile_configs(configs) -> None:
@@ -341,6 +343,21 @@ def bsi_field_adjoint_batched(grads, spacings, outs=None, workspace=None, stream
     return outs
 
 
+def bsi_scalar_forward(coeff, shape, spacing, out=None, out_dtype=torch.float32, stream=None):
+    """Scalar BSI (image interpolation / zooming): [Z, Y, X] from a one-channel
+    control grid ``coeff`` [nz, ny, nx] (Eq. 1 with one channel)."""
+    shape = tuple(int(s) for s in shape)
+    _need(coeff, "coeff", torch.float32, grid_shape(shape, spacing))
+    if out is None:
+        out = torch.empty(shape, dtype=out_dtype, device=coeff.device)
+    _need(out, "out", out.dtype, shape)
+    g = make_geom(shape, spacing)
+    st = library().bsi_scalar_forward(ctypes.byref(g), coeff.data_ptr(), out.data_ptr(), _out_dtype_code(out.dtype),
+                                      _stream(stream, coeff.device))
+    _check(st, "bsi_scalar_forward")
+    return out
+
+
 def _floating(image):
     _need(image, "image", torch.float32, tuple(image.shape))
     if image.dim() != 3:
@@ -412,9 +429,11 @@ def bsi_check_device_status(stream=None, device=None) -> int:
 
 def bsi_selfcheck_ranges(shapes, spacings, op: str = "forward", cover: bool = True):
     """Host-only range check of every kernel access for a planned call (no GPU).
-    ``op`` is "forward", "forward_bf16", "adjoint", "resample" or "resample_grad".
+    ``op`` is "forward", "forward_bf16", "adjoint", "resample", "resample_grad", "scalar" or
+    "scalar_bf16".
     Returns (violations, message)."""
-    code = {"forward": 0, "forward_bf16": 1, "adjoint": 2, "resample": 3, "resample_grad": 4}[op]
+    code = {"forward": 0, "forward_bf16": 1, "adjoint": 2, "resample": 3, "resample_grad": 4, "scalar": 5,
+            "scalar_bf16": 6}[op]
     arr = _instances([tuple(s) for s in shapes], spacings)
     buf = ctypes.create_string_buffer(256)
     n = library().bsi_selfcheck_ranges(arr, len(shapes), code, int(cover), buf, 256)

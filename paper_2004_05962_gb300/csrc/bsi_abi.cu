@@ -718,6 +718,10 @@ static bsi_status run_resample(const bsi_geom* g, const float* phi, const float*
 
 static size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Strip width of the scalar forward: a row of 4-byte (FP32) voxels starts on a
+// 16-byte boundary when x0 and X are multiples of 4 -- the rule of the 3-channel
+// field (12-byte voxels) -- so fwd_strip_tiles applies unchanged.
+
 }  // namespace bsi
 
 using namespace bsi;
@@ -845,6 +849,31 @@ bsi_status bsi_check_device_status(bsi_stream_t stream, uint32_t* flags) {
     return w ? BSI_ERR_DEVICE_STATUS : BSI_OK;
 }
 
+bsi_status bsi_scalar_forward(const bsi_geom* g, const float* coeff, void* out, bsi_dtype out_dtype,
+                              bsi_stream_t stream) {
+    bsi_status st = check_geom(g);
+    if (st != BSI_OK) return st;
+    if (out_dtype != BSI_F32 && out_dtype != BSI_BF16) return BSI_ERR_DTYPE;
+    if (empty_volume(*g)) return BSI_OK;
+    if (!coeff || !out) return BSI_ERR_NULL;
+    if (misaligned(coeff, 4) || misaligned(out, out_dtype == BSI_BF16 ? 2 : 4)) return BSI_ERR_ALIGN;
+    InstDesc d;
+    fill_desc(d, *g, false, out_dtype == BSI_BF16);
+    d.phi = coeff;
+    d.field = out;
+    Group grp;
+    grp.generic = d.dx > kMaxSpecializedDx;
+    grp.dxmax = d.dx;
+    grp.warps_req = d.warps_req;
+    grp.inst.push_back(d);
+    Batch<1> b;
+    to_batch(grp, b);
+    (void)cudaGetLastError();
+    const cudaError_t e = launch_forward_scalar(b, out_dtype == BSI_BF16, grp.generic, reinterpret_cast<cudaStream_t>(stream),
+                                                nullptr);
+    return e == cudaSuccess ? BSI_OK : cuda_fail(e);
+}
+
 bsi_status bsi_resample_forward(const bsi_geom* g, const float* phi, const float* floating, int64_t fX, int64_t fY,
                                 int64_t fZ, float* warped, bsi_stream_t stream) {
     bsi_status st = check_geom(g);
@@ -893,13 +922,14 @@ int bsi_version(void) { return 100; }
 // Host-only: plans the launches of a batched call exactly as the entry points
 // do and checks every global and shared-memory range the kernels will touch
 // (see RangeChecker).  op: 0 forward F32, 1 forward BF16, 2 adjoint, 3 / 4
-// resampling value / gradient mode (the forward's walk).  With
+// resampling value / gradient mode (the forward's walk), 5 / 6 scalar forward
+// F32 / BF16.  With
 // cover != 0 it also checks that forward rows tile each field exactly once and
 // that the reduce reads only partials phase 1 writes (memory ~ field size).
 // Returns the number of violations; the first is described in msg.
 int bsi_selfcheck_ranges(const bsi_instance* inst, int n, int op, int cover, char* msg, size_t msg_len) {
     RangeChecker rc;
-    if (n < 0 || (n > 0 && !inst) || op < 0 || op > 4) {
+    if (n < 0 || (n > 0 && !inst) || op < 0 || op > 6) {
         rc.fail("bad arguments", n, op);
     } else {
         bool ok = true;
@@ -907,13 +937,13 @@ int bsi_selfcheck_ranges(const bsi_instance* inst, int n, int op, int cover, cha
         if (!ok) {
             rc.fail("invalid geometry", n, 0);
         } else if (op != 2) {
-            std::vector<InstDesc> all = descs(inst, n, false, op == 1);
+            std::vector<InstDesc> all = descs(inst, n, false, op == 1 || op == 6);
             all.erase(std::remove_if(all.begin(), all.end(), [](const InstDesc& d) { return d.units == 0; }),
                       all.end());
             for (const Group& g : plan(all, nullptr)) {
-                // staging bytes per voxel: the field (12 FP32, 6 BF16), or T for both
-                // resampling modes (12)
-                check_forward_group(g, op == 1 ? 6 : 12, rc, cover != 0);
+                // staging bytes per voxel: the field (12 FP32, 6 BF16), T for both
+                // resampling modes (12), the scalar forward (4 FP32, 2 BF16)
+                check_forward_group(g, op == 1 ? 6 : op == 5 ? 4 : op == 6 ? 2 : 12, rc, cover != 0);
                 long long total = 0;
                 for (const InstDesc& d : g.inst) total += d.units;
                 if (cover) check_slots(total, rc);

@@ -11,7 +11,7 @@ static __device__ unsigned g_err;
 // a CTA take neighbouring units).  The per-unit work is near-uniform,
 // so the static assignment balances without an atomic ticket and is
 // deterministic.
-template <int MAXB, bool BF16, bool GENERIC>
+template <int MAXB, bool BF16, bool GENERIC, int C = 3>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
     bsi_forward_kernel(const __grid_constant__ Batch<MAXB> b) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -28,17 +28,17 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
         const InstDesc& d = b.inst[ii];
         const long long ul = uu - d.unit_begin;
         if (GENERIC) {
-            forward_unit<0, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err);
+            forward_unit<0, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err);
         } else {
             switch (d.dx) {
-                case 1: forward_unit<1, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
-                case 2: forward_unit<2, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
-                case 3: forward_unit<3, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
-                case 4: forward_unit<4, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
-                case 5: forward_unit<5, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
-                case 6: forward_unit<6, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
-                case 7: forward_unit<7, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
-                default: forward_unit<8, BF16>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 1: forward_unit<1, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 2: forward_unit<2, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 3: forward_unit<3, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 4: forward_unit<4, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 5: forward_unit<5, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 6: forward_unit<6, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 7: forward_unit<7, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                default: forward_unit<8, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
             }
         }
     }
@@ -47,9 +47,9 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
     __syncwarp();
 }
 
-template <int MAXB, bool BF16, bool GENERIC>
+template <int MAXB, bool BF16, bool GENERIC, int C = 3>
 static cudaError_t launch_fwd_t(const Batch<MAXB>& b, cudaStream_t s, LaunchInfo* info) {
-    auto kern = bsi_forward_kernel<MAXB, BF16, GENERIC>;
+    auto kern = bsi_forward_kernel<MAXB, BF16, GENERIC, C>;
     const int wpc = warps_per_cta(fwd_warp_smem(b.buf_bytes), b.warps_req);
     const int threads = wpc * kLanes;
     const int smem = wpc * fwd_warp_smem(b.buf_bytes);
@@ -70,6 +70,13 @@ cudaError_t launch_forward(const Batch<MAXB>& b, bool bf16, bool generic, cudaSt
                            LaunchInfo* info) {
     if (bf16) return generic ? launch_fwd_t<MAXB, true, true>(b, s, info) : launch_fwd_t<MAXB, true, false>(b, s, info);
     return generic ? launch_fwd_t<MAXB, false, true>(b, s, info) : launch_fwd_t<MAXB, false, false>(b, s, info);
+}
+
+// Scalar (one-channel) interpolation of a single volume.
+cudaError_t launch_forward_scalar(const Batch<1>& b, bool bf16, bool generic, cudaStream_t s, LaunchInfo* info) {
+    if (bf16)
+        return generic ? launch_fwd_t<1, true, true, 1>(b, s, info) : launch_fwd_t<1, true, false, 1>(b, s, info);
+    return generic ? launch_fwd_t<1, false, true, 1>(b, s, info) : launch_fwd_t<1, false, false, 1>(b, s, info);
 }
 
 template cudaError_t launch_forward<1>(const Batch<1>&, bool, bool, cudaStream_t, LaunchInfo*);

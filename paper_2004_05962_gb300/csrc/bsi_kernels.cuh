@@ -63,18 +63,14 @@ enum : unsigned {
 __device__ __forceinline__ uintptr_t floor16(uintptr_t a) { return a & ~(uintptr_t)15; }
 __device__ __forceinline__ uintptr_t ceil16(uintptr_t a) { return (a + 15) & ~(uintptr_t)15; }
 
-// Stores one voxel's three channels at shared address s (FP32, or BF16 rounded
-// to nearest even).
-template <bool BF16>
-__device__ __forceinline__ void put3(uint32_t s, float a, float b, float c) {
-    if (BF16) {
-        sts_b16(s, __bfloat16_as_ushort(__float2bfloat16_rn(a)));
-        sts_b16(s + 2, __bfloat16_as_ushort(__float2bfloat16_rn(b)));
-        sts_b16(s + 4, __bfloat16_as_ushort(__float2bfloat16_rn(c)));
-    } else {
-        sts_f32(s, a);
-        sts_f32(s + 4, b);
-        sts_f32(s + 8, c);
+// Stores one voxel's C channels at shared address s (FP32, or BF16 rounded to
+// nearest even).
+template <bool BF16, int C>
+__device__ __forceinline__ void put_voxel(uint32_t s, const float (&v)[C]) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        if (BF16) sts_b16(s + 2 * c, __bfloat16_as_ushort(__float2bfloat16_rn(v[c])));
+        else sts_f32(s + 4 * c, v[c]);
     }
 }
 
@@ -112,23 +108,24 @@ __device__ __forceinline__ void store_row(const unsigned char* sb, unsigned char
     }
 }
 
-// x-stage of one voxel of a tile: out = sum_l B_l(r/dx) p_l, per channel,
-// staged at shared address s.
-template <bool BF16>
-__device__ __forceinline__ void emit_voxel(uint32_t s, int wo, const float (&p0)[3], const float (&p1)[3],
-                                           const float (&p2)[3], const float (&p3)[3]) {
+// x-stage of one voxel of a tile: out = sum_l B_l(r/dx) p_l, per channel (C of
+// them: 3 for the displacement field, 1 for scalar interpolation), staged at
+// shared address s.
+template <bool BF16, int C>
+__device__ __forceinline__ void emit_voxel(uint32_t s, int wo, const float (&p0)[C], const float (&p1)[C],
+                                           const float (&p2)[C], const float (&p3)[C]) {
     const float w0 = c_lut.w[wo], w1 = c_lut.w[wo + 1], w2 = c_lut.w[wo + 2], w3 = c_lut.w[wo + 3];
-    const float v0 = fmaf(w3, p3[0], fmaf(w2, p2[0], fmaf(w1, p1[0], w0 * p0[0])));
-    const float v1 = fmaf(w3, p3[1], fmaf(w2, p2[1], fmaf(w1, p1[1], w0 * p0[1])));
-    const float v2 = fmaf(w3, p3[2], fmaf(w2, p2[2], fmaf(w1, p1[2], w0 * p0[2])));
-    put3<BF16>(s, v0, v1, v2);
+    float v[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) v[c] = fmaf(w3, p3[c], fmaf(w2, p2[c], fmaf(w1, p1[c], w0 * p0[c])));
+    put_voxel<BF16, C>(s, v);
 }
 
-// Shared-memory vector width (floats) for staging the 3 DX FP32 values of one
-// lane's tile: a lane's tile starts 12 DX bytes after its neighbour's, so with
+// Shared-memory vector width (floats) for staging the C DX FP32 values of one
+// lane's tile: a lane's tile starts 4 C DX bytes after its neighbour's, so with
 // DX a multiple of 4 (2) and an aligned row start it can move 16 (8) bytes per
 // access -- 4 (2) times fewer LDS/STS, and for DX = 4, 6, 8 fewer bank
-// conflicts than the 12 DX-byte scalar stride.
+// conflicts than the 4 C DX-byte scalar stride (C = 1 or 3, odd).
 template <int DX>
 __host__ __device__ constexpr int tile_vec() {
     return DX <= 0 ? 1 : (DX % 4 == 0 ? 4 : (DX % 2 == 0 ? 2 : 1));
@@ -136,25 +133,26 @@ __host__ __device__ constexpr int tile_vec() {
 
 // x-stage of a whole tile of DX voxels staged from shared address sv, with
 // VW-float stores (VW > 1: FP32 only, sv aligned to 4 VW bytes).
-template <int DX, int VW, bool BF16>
-__device__ __forceinline__ void emit_tile(uint32_t sv, const float (&p0)[3], const float (&p1)[3],
-                                          const float (&p2)[3], const float (&p3)[3]) {
+template <int DX, int VW, bool BF16, int C>
+__device__ __forceinline__ void emit_tile(uint32_t sv, const float (&p0)[C], const float (&p1)[C],
+                                          const float (&p2)[C], const float (&p3)[C]) {
     constexpr int ES = BF16 ? 2 : 4;
     if (VW == 1) {
 #pragma unroll
-        for (int r = 0; r < DX; ++r) emit_voxel<BF16>(sv + 3 * ES * r, weight_base(DX) + 4 * r, p0, p1, p2, p3);
+        for (int r = 0; r < DX; ++r)
+            emit_voxel<BF16, C>(sv + C * ES * r, weight_base(DX) + 4 * r, p0, p1, p2, p3);
     } else {
-        float v[3 * DX];
+        float v[C * DX];
 #pragma unroll
         for (int r = 0; r < DX; ++r) {
             const int wo = weight_base(DX) + 4 * r;
             const float w0 = c_lut.w[wo], w1 = c_lut.w[wo + 1], w2 = c_lut.w[wo + 2], w3 = c_lut.w[wo + 3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                v[3 * r + c] = fmaf(w3, p3[c], fmaf(w2, p2[c], fmaf(w1, p1[c], w0 * p0[c])));
+            for (int c = 0; c < C; ++c)
+                v[C * r + c] = fmaf(w3, p3[c], fmaf(w2, p2[c], fmaf(w1, p1[c], w0 * p0[c])));
         }
 #pragma unroll
-        for (int i = 0; i < 3 * DX / VW; ++i) {
+        for (int i = 0; i < C * DX / VW; ++i) {
             if (VW == 4) sts_v4_f32(sv + 16 * i, v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
             else sts_v2_f32(sv + 8 * i, v[2 * i], v[2 * i + 1]);
         }
@@ -164,34 +162,47 @@ __device__ __forceinline__ void emit_tile(uint32_t sv, const float (&p0)[3], con
 // One forward unit: tile-plane kz, tile-row jy, x-group xg.  DX > 0 is a
 // compile-time x-spacing (unrolled inner loop, weights as constant operands);
 // DX == 0 reads the spacing at run time.  ring is the warp's next staging
-// buffer in its store ring (0 .. kStoreStages - 1).
-template <int DX, bool BF16>
+// buffer in its store ring (0 .. kStoreStages - 1).  C channels per control
+// point and voxel: 3 (the displacement field) or 1 (scalar interpolation,
+// layouts [nz][ny][nx] and [Z][Y][X]).
+template <int DX, bool BF16, int C = 3>
 __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, unsigned char* stage,
                                              int buf_bytes, int lane, int& ring, unsigned* err) {
+    static_assert(C == 1 || C == 3, "one (scalar) or three (displacement) channels");
     constexpr int ES = BF16 ? 2 : 4;
     const int dx = DX > 0 ? DX : d.dx;
     const FwdUnit u = fwd_unit(d, ul);
     const int col = u.cell0 + lane;
 
-    // 4 (z) x 4 (y) neighbourhood column of control displacements, 3 channels.
-    float ph[4][4][3];
+    // 4 (z) x 4 (y) neighbourhood column of control points, C channels.
+    float ph[4][4][C];
 #pragma unroll
     for (int n = 0; n < 4; ++n)
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            float a = 0.f, b = 0.f, c = 0.f;
-            if (col < d.nx) {
-                const long long e = phi_elem(d, u.kz + n, u.jy + m, col);
-                BSI_GUARD(e >= 0 && e + 3 <= 3LL * d.nx * d.ny * d.nz, kErrPhiRead, err) {
-                    const float* p = d.phi + e;
-                    a = __ldg(p);
-                    b = __ldg(p + 1);
-                    c = __ldg(p + 2);
+            if (C == 3) {
+                float a = 0.f, b = 0.f, c = 0.f;
+                if (col < d.nx) {
+                    const long long e = phi_elem(d, u.kz + n, u.jy + m, col);
+                    BSI_GUARD(e >= 0 && e + 3 <= 3LL * d.nx * d.ny * d.nz, kErrPhiRead, err) {
+                        const float* p = d.phi + e;
+                        a = __ldg(p);
+                        b = __ldg(p + 1);
+                        c = __ldg(p + 2);
+                    }
                 }
+                ph[n][m][0] = a;
+                ph[n][m][C > 1 ? 1 : 0] = b;
+                ph[n][m][C > 2 ? 2 : 0] = c;
+            } else {
+                float a = 0.f;
+                if (col < d.nx) {
+                    const long long e = ((long long)(u.kz + n) * d.ny + (u.jy + m)) * d.nx + col;
+                    BSI_GUARD(e >= 0 && e < (long long)d.nx * d.ny * d.nz, kErrPhiRead, err) { a = __ldg(d.phi + e); }
+                }
+#pragma unroll
+                for (int c = 0; c < C; ++c) ph[n][m][c] = a;
             }
-            ph[n][m][0] = a;
-            ph[n][m][1] = b;
-            ph[n][m][2] = c;
         }
 
     const int z0 = u.kz * d.dz, zn = imin(d.dz, d.Z - z0);
@@ -200,28 +211,29 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
     const int xl = lane * dx;                 // first strip voxel of this lane's tile
     // voxels of this lane's tile inside the strip (0 for the halo lanes)
     const int rn = lane < u.ncell ? imin(dx, u.nvox - xl) : 0;
-    const int nbytes = u.nvox * 3 * ES;
-    const long long row_pitch = 3LL * d.X * ES;          // bytes from row y to row y + 1
+    const int nbytes = u.nvox * C * ES;
+    const long long row_pitch = (long long)C * d.X * ES;   // bytes from row y to row y + 1
     const long long plane_pitch = row_pitch * d.Y;       // bytes from plane z to plane z + 1
-    unsigned char* gplane = static_cast<unsigned char*>(d.field) + field_elem(d, z0, y0, u.x0) * ES;
+    unsigned char* gplane =
+        static_cast<unsigned char*>(d.field) + ((((long long)z0 * d.Y + y0) * d.X + u.x0) * C) * ES;   // field_elem for C
 
     for (int rz = 0; rz < zn; ++rz, gplane += plane_pitch) {
         const float a0 = c_lut.w[wzb + 4 * rz], a1 = c_lut.w[wzb + 4 * rz + 1];
         const float a2 = c_lut.w[wzb + 4 * rz + 2], a3 = c_lut.w[wzb + 4 * rz + 3];
-        float pz[4][3];
+        float pz[4][C];
 #pragma unroll
         for (int m = 0; m < 4; ++m)
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
+            for (int c = 0; c < C; ++c)
                 pz[m][c] = fmaf(a3, ph[3][m][c], fmaf(a2, ph[2][m][c], fmaf(a1, ph[1][m][c], a0 * ph[0][m][c])));
 
         unsigned char* g = gplane;
         for (int ry = 0; ry < yn; ++ry, g += row_pitch) {
             const float b0 = c_lut.w[wyb + 4 * ry], b1 = c_lut.w[wyb + 4 * ry + 1];
             const float b2 = c_lut.w[wyb + 4 * ry + 2], b3 = c_lut.w[wyb + 4 * ry + 3];
-            float p0[3], p1[3], p2[3], p3[3];
+            float p0[C], p1[C], p2[C], p3[C];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
+            for (int c = 0; c < C; ++c) {
                 p0[c] = fmaf(b3, pz[3][c], fmaf(b2, pz[2][c], fmaf(b1, pz[1][c], b0 * pz[0][c])));
                 p1[c] = __shfl_down_sync(kFull, p0[c], 1);
                 p2[c] = __shfl_down_sync(kFull, p0[c], 2);
@@ -232,24 +244,26 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
             unsigned char* sb = stage + ring * buf_bytes + shift;
             ring = ring == kStoreStages - 1 ? 0 : ring + 1;
             // (the ring buffer is free: store_row of the previous row waited for it)
-            BSI_GUARD(shift + (DX > 0 ? 3 * ES * kLanes * DX : nbytes) <= buf_bytes, kErrStage, err) {
+            BSI_GUARD(shift + (DX > 0 ? C * ES * kLanes * DX : nbytes) <= buf_bytes, kErrStage, err) {
                 // shared address of this lane's first voxel
-                const uint32_t sv = smem_u32(sb) + (uint32_t)(3 * ES * xl);
+                const uint32_t sv = smem_u32(sb) + (uint32_t)(C * ES * xl);
                 if (DX > 0) {
                     // every lane stages all DX voxels of its tile, unpredicated: a cut or
                     // halo tile lands past the row end, inside the buffer (lane 31 ends at
                     // 32 DX voxels), and only [shift, shift + nbytes) is copied out
                     constexpr int DXS = DX > 0 ? DX : 1;
                     constexpr int VW = BF16 ? 1 : tile_vec<DXS>();
-                    if (VW > 1 && (shift & (4 * VW - 1)) == 0) emit_tile<DXS, VW, BF16>(sv, p0, p1, p2, p3);
-                    else emit_tile<DXS, 1, BF16>(sv, p0, p1, p2, p3);
+                    if (VW > 1 && (shift & (4 * VW - 1)) == 0) emit_tile<DXS, VW, BF16, C>(sv, p0, p1, p2, p3);
+                    else emit_tile<DXS, 1, BF16, C>(sv, p0, p1, p2, p3);
                 } else {
-                    for (int r = 0; r < rn; ++r) emit_voxel<BF16>(sv + 3 * ES * r, wxb + 4 * r, p0, p1, p2, p3);
+                    for (int r = 0; r < rn; ++r)
+                        emit_voxel<BF16, C>(sv + C * ES * r, wxb + 4 * r, p0, p1, p2, p3);
                 }
             }
             fence_proxy_async_smem();  // this lane's staging writes before the bulk copy reads them
             __syncwarp();
-            BSI_GUARD((g - static_cast<unsigned char*>(d.field)) / ES + 3LL * u.nvox <= 3LL * d.X * d.Y * d.Z &&
+            BSI_GUARD((g - static_cast<unsigned char*>(d.field)) / ES + (long long)C * u.nvox <=
+                              (long long)C * d.X * d.Y * d.Z &&
                           g >= static_cast<unsigned char*>(d.field) && shift + nbytes <= buf_bytes,
                       kErrFieldWrite, err) {
                 store_row<ES>(sb, g, shift, nbytes, lane);

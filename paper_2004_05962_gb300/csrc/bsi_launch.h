@@ -21,6 +21,9 @@ template <int MAXB>
 cudaError_t launch_forward(const Batch<MAXB>& b, bool bf16, bool generic, cudaStream_t s,
                            LaunchInfo* info);
 
+// Scalar (one-channel) interpolation: Eq. 1 with grid [nz][ny][nx], output [Z][Y][X].
+cudaError_t launch_forward_scalar(const Batch<1>& b, bool bf16, bool generic, cudaStream_t s, LaunchInfo* info);
+
 template <int MAXB>
 cudaError_t launch_adjoint_partials(const Batch<MAXB>& b, bool generic, float* part,
                                     long long ws_floats, cudaStream_t s, LaunchInfo* info);

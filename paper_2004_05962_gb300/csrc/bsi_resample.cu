@@ -139,9 +139,9 @@ __device__ __forceinline__ void resample_unit(const InstDesc& d, long long ul, u
             if (DX > 0) {
                 constexpr int DXS = DX > 0 ? DX : 1;
                 constexpr int VW = tile_vec<DXS>();
-                emit_tile<DXS, VW, false>(sv, p0, p1, p2, p3);   // every lane, past the row end too
+                emit_tile<DXS, VW, false, 3>(sv, p0, p1, p2, p3);   // every lane, past the row end too
             } else {
-                for (int r = 0; r < rn; ++r) emit_voxel<false>(sv + 12u * r, wxb + 4 * r, p0, p1, p2, p3);
+                for (int r = 0; r < rn; ++r) emit_voxel<false, 3>(sv + 12u * r, wxb + 4 * r, p0, p1, p2, p3);
             }
             __syncwarp();
             const int y = y0 + ry, z = z0 + rz;

@@ -148,14 +148,15 @@ EDGE_CASES = [
 ]
 
 
-@pytest.mark.parametrize("op", ["forward", "forward_bf16", "adjoint", "resample", "resample_grad"])
+@pytest.mark.parametrize("op", ["forward", "forward_bf16", "adjoint", "resample", "resample_grad", "scalar",
+                                "scalar_bf16"])
 def test_selfcheck_edge_cases(lib, op):
     for shape, spacing in EDGE_CASES:
         n, msg = P.bsi_selfcheck_ranges([shape], [spacing], op, cover=True)
         assert n == 0, (shape, spacing, msg)
 
 
-@pytest.mark.parametrize("op", ["forward", "adjoint", "resample", "resample_grad"])
+@pytest.mark.parametrize("op", ["forward", "adjoint", "resample", "resample_grad", "scalar", "scalar_bf16"])
 def test_selfcheck_random_geometries(lib, op):
     rng = np.random.default_rng(7)
     for _ in range(60):
@@ -221,3 +222,16 @@ def test_resample_validation_before_cuda(lib):
     assert rb(ctypes.byref(g), fake, fake, 40, 30, 20, fake, None, fake, need, None) == 1
     e, _ = _geom(0, 30, 20, 5, 4, 3)
     assert lib.bsi_resample_backward_workspace_bytes(ctypes.byref(e)) == 0
+
+
+def test_scalar_validation_before_cuda(lib):
+    fake = 0x7F0000000000  # never dereferenced: validation fails first
+    g, _ = _geom(40, 30, 20, 5, 4, 3)
+    sf = lib.bsi_scalar_forward
+    assert sf(ctypes.byref(g), None, fake, 0, None) == 1
+    assert sf(ctypes.byref(g), fake, None, 0, None) == 1
+    assert sf(ctypes.byref(g), fake + 2, fake, 0, None) == 6
+    assert sf(ctypes.byref(g), fake, fake + 2, 0, None) == 6
+    assert sf(ctypes.byref(g), fake, fake, 7, None) == 5
+    e, _ = _geom(0, 30, 20, 5, 4, 3)
+    assert sf(ctypes.byref(e), None, None, 0, None) == 0
