@@ -394,6 +394,26 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
 
     res["resample"] = measure_resample(P, synth, model, dev, s, phi, field, dphi, hbm_peak, iters)
 
+    # the paper's thread-per-tile formulations (TT, TTLI) on the same volume
+    pv = {}
+    for v in ("tt", "ttli"):
+        t = time_fn(lambda: P.bsi_field_forward_variant(phi, shape, spacing, v, out=field), s, 5)
+        pv[v] = {"ms": round(t, 5), "gvox_s": round(nvox / t / 1e6, 2)}
+    pv["separable_ms"] = res["components"]["fwd_f32"]["ms"]
+    res["paper_tile_variants"] = pv
+
+    # scalar BSI: a 4x zoom of a 128 x 128 x 75 image (its samples as control
+    # points, one border sample below and two above) into the 512 x 512 x 300 volume
+    zshape, zsp = (300, 512, 512), (4, 4, 4)
+    img = torch.from_numpy(synth.blob_image(synth.grid_shape(zshape, zsp), seed=7)).to(dev)
+    zout = torch.empty(zshape, device=dev)
+    ms_z = time_fn(lambda: P.bsi_scalar_forward(img, zshape, zsp, out=zout), s, iters)
+    zb = 4 * int(np.prod(zshape)) + 4 * img.numel()
+    res["scalar_zoom"] = {"ms": round(ms_z, 5), "gvox_s": round(nvox / ms_z / 1e6, 2), "gbs": round(zb / ms_z / 1e6, 1),
+                          "frac_of_hbm": round(zb / ms_z / 1e6 / hbm_peak, 4),
+                          "workload": "4x zoom of a 78 x 131 x 131 grid (128 x 128 x 75 image + border) to 512 x 512 x 300, FP32"}
+    del img, zout
+
     # 512^3 spacing sweep (forward FP32)
     sweep = {}
     big = (512, 512, 512)

@@ -217,6 +217,23 @@ bsi_status bsi_check_device_status(bsi_stream_t stream, uint32_t* flags);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int bsi_version(void);
 
+/* The paper's own GPU formulations of Eq. 1, for its accuracy comparison
+ * (Sec. 5.3) and as a measured contrast to the separable kernel:
+ *   BSI_VARIANT_SEPARABLE  bsi_field_forward's strip kernel (FP32 output)
+ *   BSI_VARIANT_TT         thread per tile (Sec. 3.2): the 64-term sum of Eq. 1
+ *                          per channel, the cell's control points in registers
+ *   BSI_VARIANT_TTLI       thread per tile with linear interpolations (Sec. 3.3,
+ *                          App. B): 8 trilinear interpolations of 2x2x2
+ *                          sub-cubes and one of their results, each lerp an FMA
+ * phi and field as for bsi_field_forward (field FP32).  TT and TTLI take
+ * spacings up to 32 (BSI_ERR_SPACING); an unknown variant is BSI_ERR_DTYPE.
+ * TT and TTLI store each voxel from the thread that computes it, as the
+ * paper's kernels do: they are not the fast path. */
+typedef enum { BSI_VARIANT_SEPARABLE = 0, BSI_VARIANT_TT = 1, BSI_VARIANT_TTLI = 2 } bsi_variant;
+
+bsi_status bsi_field_forward_variant(const bsi_geom* g, const float* phi, float* field, int32_t variant,
+                                     bsi_stream_t stream);
+
 /* Scalar BSI: Eq. 1 with one channel, for interpolating (zooming) an image
  * whose samples serve as the control points (Sec. 7 names image
  * interpolation as another use of the method).  The same kernels as

@@ -14,6 +14,7 @@ from .bsi import (  # noqa: F401
     bsi_field_adjoint_batched,
     bsi_field_forward,
     bsi_field_forward_batched,
+    bsi_field_forward_variant,
     bsi_field_adjoint_noalloc,
     bsi_get_tile_config,
     bsi_probe_fill,

@@ -112,6 +112,7 @@ def library(checked: bool | None = None) -> ctypes.CDLL:
                                       ctypes.POINTER(BsiTileConfig)]),
         "bsi_probe_fill": (i32, [vp, sz, ctypes.c_uint32, vp]),
         "bsi_scalar_forward": (i32, [G, vp, vp, i32, vp]),
+        "bsi_field_forward_variant": (i32, [G, vp, vp, ctypes.c_int32, vp]),
         "bsi_resample_forward": (i32, [G, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp, vp]),
         "bsi_resample_backward_workspace_bytes": (sz, [G]),
         "bsi_resample_backward": (i32, [G, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp, vp, vp,
@@ -132,7 +133,7 @@ def exported_symbols():
             "bsi_check_device_status", "bsi_version", "bsi_selfcheck_ranges",
             "bsi_field_adjoint_noalloc", "bsi_set_tile_configs", "bsi_get_tile_config", "bsi_probe_fill",
             "bsi_resample_forward", "bsi_resample_backward_workspace_bytes", "bsi_resample_backward",
-            "bsi_scalar_forward"]
+            "bsi_scalar_forward", "bsi_field_forward_variant"]
 
 
 def bsi_set_tile_configs(configs) -> None:
@@ -341,6 +342,25 @@ def bsi_field_adjoint_batched(grads, spacings, outs=None, workspace=None, stream
                                              _stream(stream, dev))
     _check(st, "bsi_field_adjoint_batched")
     return outs
+
+
+VARIANTS = {"separable": 0, "tt": 1, "ttli": 2}
+
+
+def bsi_field_forward_variant(phi, shape, spacing, variant="ttli", out=None, stream=None):
+    """Dense FP32 field by one of the paper's GPU formulations ("tt": thread per
+    tile, "ttli": thread per tile with trilinear interpolations) or the
+    separable kernel ("separable")."""
+    shape = tuple(int(s) for s in shape)
+    _need(phi, "phi", torch.float32, grid_shape(shape, spacing) + (3,))
+    if out is None:
+        out = torch.empty(shape + (3,), dtype=torch.float32, device=phi.device)
+    _need(out, "out", torch.float32, shape + (3,))
+    g = make_geom(shape, spacing)
+    st = library().bsi_field_forward_variant(ctypes.byref(g), phi.data_ptr(), out.data_ptr(), VARIANTS[variant],
+                                             _stream(stream, phi.device))
+    _check(st, "bsi_field_forward_variant")
+    return out
 
 
 def bsi_scalar_forward(coeff, shape, spacing, out=None, out_dtype=torch.float32, stream=None):

@@ -838,13 +838,14 @@ bsi_status bsi_get_tile_config(int32_t dx, int32_t dy, int32_t dz, bsi_tile_conf
 
 bsi_status bsi_check_device_status(bsi_stream_t stream, uint32_t* flags) {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    static thread_local unsigned words[3];
+    static thread_local unsigned words[4];
     cudaError_t e = forward_err_read_clear(&words[0], s);
     if (e == cudaSuccess) e = adjoint_err_read_clear(&words[1], s);
     if (e == cudaSuccess) e = resample_err_read_clear(&words[2], s);
+    if (e == cudaSuccess) e = variants_err_read_clear(&words[3], s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e);
-    const uint32_t w = words[0] | words[1] | words[2];
+    const uint32_t w = words[0] | words[1] | words[2] | words[3];
     if (flags) *flags = w;
     return w ? BSI_ERR_DEVICE_STATUS : BSI_OK;
 }
@@ -871,6 +872,31 @@ bsi_status bsi_scalar_forward(const bsi_geom* g, const float* coeff, void* out, 
     (void)cudaGetLastError();
     const cudaError_t e = launch_forward_scalar(b, out_dtype == BSI_BF16, grp.generic, reinterpret_cast<cudaStream_t>(stream),
                                                 nullptr);
+    return e == cudaSuccess ? BSI_OK : cuda_fail(e);
+}
+
+bsi_status bsi_field_forward_variant(const bsi_geom* g, const float* phi, float* field, int32_t variant,
+                                     bsi_stream_t stream) {
+    if (variant == BSI_VARIANT_SEPARABLE) return bsi_field_forward(g, phi, field, BSI_F32, stream);
+    if (variant != BSI_VARIANT_TT && variant != BSI_VARIANT_TTLI) return BSI_ERR_DTYPE;
+    bsi_status st = check_geom(g);
+    if (st != BSI_OK) return st;
+    if (g->dx > 32 || g->dy > 32 || g->dz > 32) return BSI_ERR_SPACING;
+    if (empty_volume(*g)) return BSI_OK;
+    if (!phi || !field) return BSI_ERR_NULL;
+    if (misaligned(phi, 4) || misaligned(field, 4)) return BSI_ERR_ALIGN;
+    InstDesc d;
+    fill_desc(d, *g, false, false);
+    d.phi = phi;
+    d.field = field;
+    Group grp;
+    grp.dxmax = d.dx;
+    grp.inst.push_back(d);
+    Batch<1> b;
+    to_batch(grp, b);
+    (void)cudaGetLastError();
+    const cudaError_t e = launch_forward_tile_variant(b, variant == BSI_VARIANT_TTLI,
+                                                      reinterpret_cast<cudaStream_t>(stream), nullptr);
     return e == cudaSuccess ? BSI_OK : cuda_fail(e);
 }
 

@@ -21,6 +21,10 @@ template <int MAXB>
 cudaError_t launch_forward(const Batch<MAXB>& b, bool bf16, bool generic, cudaStream_t s,
                            LaunchInfo* info);
 
+// The paper's thread-per-tile kernels (TT, TTLI with lerp = true) for one volume.
+cudaError_t launch_forward_tile_variant(const Batch<1>& b, bool lerp, cudaStream_t s, LaunchInfo* info);
+cudaError_t variants_err_read_clear(unsigned* out, cudaStream_t s);
+
 // Scalar (one-channel) interpolation: Eq. 1 with grid [nz][ny][nx], output [Z][Y][X].
 cudaError_t launch_forward_scalar(const Batch<1>& b, bool bf16, bool generic, cudaStream_t s, LaunchInfo* info);
 

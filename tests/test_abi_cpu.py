@@ -235,3 +235,14 @@ def test_scalar_validation_before_cuda(lib):
     assert sf(ctypes.byref(g), fake, fake, 7, None) == 5
     e, _ = _geom(0, 30, 20, 5, 4, 3)
     assert sf(ctypes.byref(e), None, None, 0, None) == 0
+
+
+def test_variant_validation_before_cuda(lib):
+    fake = 0x7F0000000000  # never dereferenced: validation fails first
+    g, _ = _geom(40, 30, 20, 5, 4, 3)
+    fv = lib.bsi_field_forward_variant
+    assert fv(ctypes.byref(g), fake, fake, 7, None) == 5
+    assert fv(ctypes.byref(g), None, fake, 1, None) == 1
+    assert fv(ctypes.byref(g), fake, fake + 2, 2, None) == 6
+    big, _ = _geom(40, 30, 20, 33, 4, 3)
+    assert fv(ctypes.byref(big), fake, fake, 2, None) == 3

@@ -1,0 +1,59 @@
+"""The paper's thread-per-tile formulations (TT, TTLI) against the FP64 oracle,
+and the accuracy comparison of Sec. 5.3 (average absolute error of each GPU
+formulation with respect to an FP64 reference) on synthetic inputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2004_05962_gb300 as P
+from paper_2004_05962_gb300 import synth
+from gpu_util import FWD_TOL, dev
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ((64, 64, 64), (5, 5, 5)),
+    ((9, 10, 11), (2, 2, 2)),
+    ((13, 7, 40), (3, 2, 3)),
+    ((20, 11, 93), (6, 5, 5)),
+    ((16, 16, 250), (8, 8, 8)),
+    ((11, 12, 300), (4, 3, 9)),
+    ((40, 35, 70), (16, 3, 32)),
+    ((1, 1, 1), (1, 1, 1)),
+]
+
+
+@pytest.mark.parametrize("variant", ["tt", "ttli"])
+@pytest.mark.parametrize("shape,spacing", CASES, ids=[f"{s}-{d}" for s, d in CASES])
+def test_tile_variants_match_oracle(shape, spacing, variant):
+    phi = synth.uniform_phi(shape, spacing, -2, 2, seed=sum(shape) + sum(spacing))
+    got = P.bsi_field_forward_variant(torch.from_numpy(phi).to(dev()), shape, spacing, variant)
+    torch.cuda.synchronize()
+    want = oracle.forward(phi, shape, spacing)
+    err = float(np.max(np.abs(got.double().cpu().numpy() - want)))
+    assert err <= FWD_TOL * float(np.max(np.abs(phi))), err
+    assert P.bsi_check_device_status() == 0
+
+
+def test_accuracy_table():
+    """Average absolute error (x 1e-6) against the FP64 oracle, as the paper
+    tabulates it, for a 5x5x5-tile volume (NiftyReg's default) with control
+    displacements of a few voxels: every formulation stays within the FP32
+    tolerance; the numbers are printed for the record."""
+    shape, spacing = (160, 192, 192), (5, 5, 5)
+    phi = synth.gaussian_random_phi(shape, spacing, 3.0, 2.0, seed=4)
+    want = oracle.forward(phi, shape, spacing)
+    phit = torch.from_numpy(phi).to(dev())
+    rows = {}
+    for v in ("separable", "tt", "ttli"):
+        got = P.bsi_field_forward_variant(phit, shape, spacing, v).double().cpu().numpy()
+        d = np.abs(got - want)
+        rows[v] = (float(d.mean()) * 1e6, float(d.max()) * 1e6)
+        assert d.max() <= FWD_TOL * float(np.max(np.abs(phi)))
+    print("\naccuracy vs FP64 oracle (mean, max) x 1e-6:",
+          ", ".join(f"{k} {m:.3f} / {x:.3f}" for k, (m, x) in rows.items()))
+    # the paper's finding: the lerp (FMA) form is about twice as accurate as the
+    # plain triple sum (measured here 0.078 vs 0.213; the separable form 0.100)
+    assert rows["ttli"][0] < 0.75 * rows["tt"][0]
+    assert rows["separable"][0] < 0.75 * rows["tt"][0]
