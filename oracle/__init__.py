@@ -56,8 +56,10 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.bsi_oracle_adjoint_points.argtypes = geom + [vp, i32, vp, i64, vp, i32]
     lib.bsi_oracle_resample.argtypes = geom + [vp, i32, vp, i32, i64, i64, i64, vp, i32]
     lib.bsi_oracle_resample_grad.argtypes = geom + [vp, i32, vp, i32, i64, i64, i64, vp, i32, vp, i32]
+    lib.bsi_oracle_forward_rational.argtypes = [i64, i64, i64, vp, vp, vp, vp, i32, vp]
     for f in ("bsi_oracle_forward", "bsi_oracle_forward_points", "bsi_oracle_adjoint",
-              "bsi_oracle_adjoint_points", "bsi_oracle_resample", "bsi_oracle_resample_grad"):
+              "bsi_oracle_adjoint_points", "bsi_oracle_resample", "bsi_oracle_resample_grad",
+              "bsi_oracle_forward_rational"):
         getattr(lib, f).restype = i32
     return lib
 
@@ -155,6 +157,30 @@ def adjoint_points(grad, spacing, gxyz, nthreads: int = 0, lib=None) -> np.ndarr
                                        q.ctypes.data, q.shape[0], out.ctypes.data, nthreads)
     if rc:
         raise OracleError("bsi_oracle_adjoint_points: bad arguments")
+    return out
+
+
+def rational_grid_shape(shape, num, den, off):
+    """Stored grid (nz, ny, nx) for spacing num/den and lattice shift off/den per
+    axis; num, den, off are given (z, y, x) like shape."""
+    return tuple(((int(N) - 1) * int(d) + int(o)) // int(n) + 4 if int(N) > 0 else 4
+                 for N, n, d, o in zip(shape, num, den, off))
+
+
+def forward_rational(phi, shape, num, den, off, lib=None) -> np.ndarray:
+    """Eq. 1 with spacing num/den and lattice shift off/den voxels per axis
+    ((z, y, x) order like ``shape``): field [Z, Y, X, 3] (FP64)."""
+    lib = lib or load()
+    Z, Y, X = (int(s) for s in shape)
+    assert phi.shape == rational_grid_shape(shape, num, den, off) + (3,), (phi.shape, shape)
+    p, f32 = _in(phi)
+    to_xyz = lambda a: np.ascontiguousarray(np.array(a, np.int64)[::-1])
+    n3, d3, o3 = to_xyz(num), to_xyz(den), to_xyz(off)
+    out = np.empty((Z, Y, X, 3), np.float64)
+    rc = lib.bsi_oracle_forward_rational(X, Y, Z, n3.ctypes.data, d3.ctypes.data, o3.ctypes.data, p.ctypes.data,
+                                         f32, out.ctypes.data)
+    if rc:
+        raise OracleError("bsi_oracle_forward_rational: bad arguments")
     return out
 
 

@@ -520,3 +520,70 @@ int bsi_oracle_resample_grad(int64_t X, int64_t Y, int64_t Z, int dx, int dy, in
     oracle_parallel(Y * Z, bsi_oracle_threads(nthreads), rs_rows, &c);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Non-integer, non-aligned spacing (the paper's future work, Sec. 7: grids   */
+/* not aligned to the voxel grid, weights computed on the fly).               */
+/*                                                                             */
+/* Per axis the spacing is num/den voxels and the lattice is shifted by       */
+/* off/den voxels: u_x = (x * den + off) / num, cell f = floor(u_x), offset   */
+/* u = u_x - f, and Eq. 1 reads the stored columns f .. f + 3 (one border     */
+/* point below, as for integer spacing).  With den = 1, off = 0 this is the    */
+/* integer-spacing oracle above.  Grid dims: floor(((N - 1) den + off) / num)  */
+/* + 4 per axis.                                                               */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t X, Y, Z;
+    int64_t num[3], den[3], off[3];
+    int64_t n[3];
+} oracle_rgeom;
+
+static int64_t oracle_rdim(int64_t N, int64_t num, int64_t den, int64_t off) {
+    return N > 0 ? ((N - 1) * den + off) / num + 4 : 4;
+}
+
+static void oracle_raxis(int64_t x, int64_t num, int64_t den, int64_t off, int64_t* f, double* u) {
+#if ORACLE_MUTANT == 12 /* lattice shift applied with the wrong sign */
+    const double q = (double)(x * den + (off ? num - off : 0)) / (double)num;
+#else
+    const double q = (double)(x * den + off) / (double)num;
+#endif
+    const double fl = floor(q);
+    *f = (int64_t)fl;
+    *u = q - fl;
+}
+
+int bsi_oracle_forward_rational(int64_t X, int64_t Y, int64_t Z, const int64_t num[3], const int64_t den[3],
+                                const int64_t off[3], const void* phi, int in_f32, double* field) {
+    if (X < 0 || Y < 0 || Z < 0 || !num || !den || !off || !phi || (X * Y * Z > 0 && !field)) return -1;
+    oracle_rgeom g;
+    g.X = X; g.Y = Y; g.Z = Z;
+    const int64_t N[3] = {X, Y, Z};
+    for (int a = 0; a < 3; ++a) {
+        if (num[a] < 1 || den[a] < 1 || off[a] < 0 || off[a] >= num[a]) return -1;
+        g.num[a] = num[a]; g.den[a] = den[a]; g.off[a] = off[a];
+        g.n[a] = oracle_rdim(N[a], num[a], den[a], off[a]);
+    }
+    for (int64_t z = 0; z < Z; ++z)
+        for (int64_t y = 0; y < Y; ++y)
+            for (int64_t x = 0; x < X; ++x) {
+                int64_t fi, fj, fk;
+                double u, v, w, Bu[4], Bv[4], Bw[4];
+                oracle_raxis(x, g.num[0], g.den[0], g.off[0], &fi, &u);
+                oracle_raxis(y, g.num[1], g.den[1], g.off[1], &fj, &v);
+                oracle_raxis(z, g.num[2], g.den[2], g.off[2], &fk, &w);
+                oracle_basis(u, Bu);
+                oracle_basis(v, Bv);
+                oracle_basis(w, Bw);
+                double* out = field + ((z * Y + y) * X + x) * 3;
+                out[0] = out[1] = out[2] = 0.0;
+                for (int l = 0; l < 4; ++l)
+                    for (int m = 0; m < 4; ++m)
+                        for (int n = 0; n < 4; ++n) {
+                            const double wt = Bu[l] * Bv[m] * Bw[n];
+                            const int64_t idx = (((fk + n) * g.n[1] + (fj + m)) * g.n[0] + (fi + l)) * 3;
+                            for (int c = 0; c < 3; ++c) out[c] += wt * oracle_load(phi, in_f32, idx + c);
+                        }
+            }
+    return 0;
+}

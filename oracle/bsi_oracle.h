@@ -79,6 +79,15 @@ int bsi_oracle_resample_grad(int64_t X, int64_t Y, int64_t Z, int dx, int dy, in
                              int64_t fX, int64_t fY, int64_t fZ, const void* dW, int dw_f32,
                              double* G, int nthreads);
 
+/* Non-integer, non-aligned spacing (Sec. 7's future work): per axis a spacing
+ * of num/den voxels and a lattice shift of off/den voxels (0 <= off < num):
+ * u_x = (x den + off) / num, cell floor(u_x), offset u_x - floor(u_x); grid
+ * dims floor(((N-1) den + off) / num) + 4 per axis.  Arrays num, den, off are
+ * (x, y, z).  Single-threaded; den = 1, off = 0 gives bsi_oracle_forward. */
+int bsi_oracle_forward_rational(int64_t X, int64_t Y, int64_t Z, const int64_t num[3],
+                                const int64_t den[3], const int64_t off[3], const void* phi,
+                                int in_f32, double* field);
+
 #ifdef __cplusplus
 }
 #endif

@@ -433,6 +433,88 @@ def pin_resample_backward_fd(lib):
     return worst, 1e-5 * max(1.0, float(np.max(np.abs(grad))))
 
 
+# ---------------------------------------------------------------- non-integer spacing
+# Spacing num/den and lattice shift off/den voxels per axis ((z, y, x) order):
+# u = (x den + off) / num (Sec. 7's grids not aligned to the voxel grid).
+
+RATIONAL_CASES = [  # (shape, num, den, off)
+    ((7, 9, 11), (5, 7, 9), (2, 2, 2), (0, 3, 1)),        # spacings 2.5, 3.5, 4.5
+    ((6, 10, 13), (4, 3, 10), (3, 1, 3), (2, 0, 7)),       # 1.33, 3, 3.33; shifted lattices
+    ((5, 8, 9), (1, 9, 7), (1, 4, 5), (0, 8, 6)),          # 1, 2.25, 1.4
+]
+
+
+def _rat_u(N, n, d, o):
+    return (np.arange(N, dtype=np.float64) * d + o) / n
+
+
+def pin_rational_integer_case(lib):
+    """den = 1, off = 0 is integer spacing: the same values as the integer oracle."""
+    rng = _rng(41)
+    worst = 0.0
+    for shape, spacing in SMALL_CASES[:4]:
+        phi = rng.uniform(-2, 2, oracle.grid_shape(shape, spacing) + (3,))
+        a = oracle.forward(phi, shape, spacing, lib=lib)
+        b = oracle.forward_rational(phi, shape, spacing, (1, 1, 1), (0, 0, 0), lib=lib)
+        worst = max(worst, float(np.max(np.abs(a - b))))
+    return worst, 0.0
+
+
+def pin_rational_brute_force(lib):
+    """The global sum over all grid points of phi_g beta3(u - g + 1) per axis."""
+    rng = _rng(42)
+    worst = 0.0
+    for shape, num, den, off in RATIONAL_CASES:
+        grid = oracle.rational_grid_shape(shape, num, den, off)
+        phi = rng.uniform(-2, 2, grid + (3,))
+        W = [beta3(_rat_u(N, n, d, o)[:, None] - np.arange(g, dtype=np.float64)[None, :] + 1.0)
+             for N, n, d, o, g in zip(shape, num, den, off, grid)]
+        want = np.einsum("zc,yb,xa,cbad->zyxd", W[0], W[1], W[2], phi, optimize=True)
+        T = oracle.forward_rational(phi, shape, num, den, off, lib=lib)
+        worst = max(worst, float(np.max(np.abs(T - want))))
+    return worst, 1e-13
+
+
+def pin_rational_scipy(lib):
+    """scipy's tensor-product cubic B-spline (knots at the integers, starting at
+    -3) evaluated at the lattice coordinates u."""
+    from scipy.interpolate import NdBSpline
+
+    rng = _rng(43)
+    worst = 0.0
+    for shape, num, den, off in RATIONAL_CASES:
+        grid = oracle.rational_grid_shape(shape, num, den, off)
+        phi = rng.uniform(-2, 2, grid + (3,))
+        spl = NdBSpline(tuple(np.arange(g + 4, dtype=np.float64) - 3.0 for g in grid), phi, 3)
+        uz, uy, ux = (_rat_u(N, n, d, o) for N, n, d, o in zip(shape, num, den, off))
+        Z, Y, X = shape
+        z, y, x = np.meshgrid(uz, uy, ux, indexing="ij")
+        want = spl(np.stack([z, y, x], -1).reshape(-1, 3)).reshape(Z, Y, X, 3)
+        T = oracle.forward_rational(phi, shape, num, den, off, lib=lib)
+        worst = max(worst, float(np.max(np.abs(T - want))))
+    return worst, 1e-12
+
+
+def pin_rational_affine(lib):
+    """Control point g at voxel coordinate (g - 1) num/den - off/den per axis and
+    phi affine in it: T(x) = A x + b exactly (the index origin and the shift)."""
+    rng = _rng(44)
+    worst, scale = 0.0, 1.0
+    for shape, num, den, off in RATIONAL_CASES:
+        grid = oracle.rational_grid_shape(shape, num, den, off)
+        A, b = rng.uniform(-2, 2, (3, 3)), rng.uniform(-5, 5, 3)
+        pos = [(np.arange(g, dtype=np.float64) - 1.0) * n / d - o / d for g, n, d, o in zip(grid, num, den, off)]
+        gz, gy, gx = np.meshgrid(*pos, indexing="ij")
+        phi = np.stack([gx, gy, gz], -1) @ A.T + b
+        T = oracle.forward_rational(phi, shape, num, den, off, lib=lib)
+        Z, Y, X = shape
+        z, y, x = np.meshgrid(np.arange(Z), np.arange(Y), np.arange(X), indexing="ij")
+        want = np.stack([x, y, z], -1).astype(np.float64) @ A.T + b
+        worst = max(worst, float(np.max(np.abs(T - want))))
+        scale = max(scale, float(np.max(np.abs(want))))
+    return worst, 1e-13 * scale
+
+
 ALL_PINS = [
     pin_partition_of_unity,
     pin_affine_reproduction,
@@ -450,6 +532,10 @@ ALL_PINS = [
     pin_resample_affine_image,
     pin_resample_grad_scipy_fd,
     pin_resample_backward_fd,
+    pin_rational_integer_case,
+    pin_rational_brute_force,
+    pin_rational_scipy,
+    pin_rational_affine,
 ]
 
 

@@ -17,6 +17,7 @@ MUTANTS = {
     9: "resampling: x weights of the two taps exchanged",
     10: "resampling: sign of the z derivative flipped",
     11: "resampling: edge values repeated outside the image",
+    12: "non-integer spacing: lattice shift with the wrong sign",
 }
 
 
