@@ -402,6 +402,18 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
     pv["separable_ms"] = res["components"]["fwd_f32"]["ms"]
     res["paper_tile_variants"] = pv
 
+    # non-integer, non-aligned spacing: 4.7 voxels per axis, lattice shifted by
+    # 0.3 / 0 / 0.9 voxels (z, y, x), on the 512 x 512 x 300 volume
+    rn, rd, ro = (47, 47, 47), (10, 10, 10), (3, 0, 9)
+    rgrid = P.rational_grid_shape(shape, rn, rd, ro)
+    rphi = torch.rand(rgrid + (3,), device=dev) * 6.0 - 3.0
+    ms_r = time_fn(lambda: P.bsi_field_forward_rational(rphi, shape, rn, rd, ro, out=field), s, iters)
+    rb = model.forward_bytes(shape, (5, 5, 5)) - 12 * model.grid_points(shape, (5, 5, 5)) + 12 * rphi.numel() // 3
+    res["rational_forward"] = {"ms": round(ms_r, 5), "gvox_s": round(nvox / ms_r / 1e6, 2),
+                               "gbs": round(rb / ms_r / 1e6, 1), "frac_of_hbm": round(rb / ms_r / 1e6 / hbm_peak, 4),
+                               "workload": "512x512x300, spacing 4.7 voxels, lattice shift (0.3, 0, 0.9) (z, y, x), FP32"}
+    del rphi
+
     # scalar BSI: a 4x zoom of a 128 x 128 x 75 image (its samples as control
     # points, one border sample below and two above) into the 512 x 512 x 300 volume
     zshape, zsp = (300, 512, 512), (4, 4, 4)

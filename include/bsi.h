@@ -217,6 +217,42 @@ bsi_status bsi_check_device_status(bsi_stream_t stream, uint32_t* flags);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int bsi_version(void);
 
+/* ------------------------------------------------------------------------
+ * Non-integer, non-aligned spacing (Sec. 7 leaves control grids that are not
+ * aligned to the voxel grid to future work, noting the weights must then be
+ * computed on the fly).  Per axis (x, y, z) the spacing is num/den voxels and
+ * the lattice is shifted by off/den voxels: voxel x has
+ *   q = x den + off,  cell f = floor(q / num),  offset u = (q - f num) / num,
+ * and Eq. 1 reads stored columns f .. f + 3 (the one-point border below, as
+ * for integer spacing; den = 1, off = 0 is integer spacing).  Control point g
+ * sits at voxel coordinate (g - 1) num/den - off/den.  Grid dims per axis:
+ *   floor(((N - 1) den + off) / num) + 4.
+ * Limits: 1 <= den <= BSI_MAX_RATIONAL_DEN, den <= num <= 64 den (spacing
+ * 1..64), 0 <= off < num (BSI_ERR_SPACING); nx <= BSI_MAX_RATIONAL_NX (one
+ * row of y/z-contracted columns lives in shared memory; BSI_ERR_DIMS).
+ * ------------------------------------------------------------------------ */
+#define BSI_MAX_RATIONAL_DEN 1024
+#define BSI_MAX_RATIONAL_NX 16384
+
+typedef struct {
+    int64_t X, Y, Z;
+    int32_t num[3], den[3], off[3];   /* (x, y, z) */
+    int64_t nx, ny, nz;               /* stored grid, from bsi_geom_rational_init */
+} bsi_geom_rational;
+
+/* Fills g and its grid dims; BSI_ERR_DIMS / BSI_ERR_SPACING / BSI_ERR_NULL. */
+bsi_status bsi_geom_rational_init(bsi_geom_rational* g, int64_t X, int64_t Y, int64_t Z, const int32_t num[3],
+                                  const int32_t den[3], const int32_t off[3]);
+
+/* Eq. 1 on such a grid, weights computed per voxel from the exact offset
+ * (rounded once to FP32), FP32 output.
+ *   phi   : device, FP32 [nz][ny][nx][3], read only
+ *   field : device, FP32 [Z][Y][X][3], fully overwritten
+ * BSI_ERR_GRID_MISMATCH if g's grid dims differ from the formula above; other
+ * checks as bsi_field_forward.  One launch on `stream`. */
+bsi_status bsi_field_forward_rational(const bsi_geom_rational* g, const float* phi, float* field,
+                                      bsi_stream_t stream);
+
 /* The paper's own GPU formulations of Eq. 1, for its accuracy comparison
  * (Sec. 5.3) and as a measured contrast to the separable kernel:
  *   BSI_VARIANT_SEPARABLE  bsi_field_forward's strip kernel (FP32 output)

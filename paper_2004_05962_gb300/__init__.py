@@ -14,6 +14,7 @@ from .bsi import (  # noqa: F401
     bsi_field_adjoint_batched,
     bsi_field_forward,
     bsi_field_forward_batched,
+    bsi_field_forward_rational,
     bsi_field_forward_variant,
     bsi_field_adjoint_noalloc,
     bsi_get_tile_config,
@@ -26,6 +27,7 @@ from .bsi import (  # noqa: F401
     bsi_set_tile_configs,
     bsi_tile_configs,
     grid_shape,
+    rational_grid_shape,
     library,
 )
 from .autograd import BSIField, BSIResample, field, resample  # noqa: F401

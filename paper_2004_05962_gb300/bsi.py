@@ -48,6 +48,12 @@ class BsiGeom(ctypes.Structure):
                 ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64)]
 
 
+class BsiGeomRational(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_int64), ("Y", ctypes.c_int64), ("Z", ctypes.c_int64),
+                ("num", ctypes.c_int32 * 3), ("den", ctypes.c_int32 * 3), ("off", ctypes.c_int32 * 3),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64)]
+
+
 class BsiInstance(ctypes.Structure):
     _fields_ = [("geom", BsiGeom), ("phi", ctypes.c_void_p), ("field", ctypes.c_void_p),
                 ("grad_field", ctypes.c_void_p), ("grad_phi", ctypes.c_void_p)]
@@ -113,6 +119,9 @@ def library(checked: bool | None = None) -> ctypes.CDLL:
         "bsi_probe_fill": (i32, [vp, sz, ctypes.c_uint32, vp]),
         "bsi_scalar_forward": (i32, [G, vp, vp, i32, vp]),
         "bsi_field_forward_variant": (i32, [G, vp, vp, ctypes.c_int32, vp]),
+        "bsi_geom_rational_init": (i32, [ctypes.POINTER(BsiGeomRational), ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_int64, vp, vp, vp]),
+        "bsi_field_forward_rational": (i32, [ctypes.POINTER(BsiGeomRational), vp, vp, vp]),
         "bsi_resample_forward": (i32, [G, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp, vp]),
         "bsi_resample_backward_workspace_bytes": (sz, [G]),
         "bsi_resample_backward": (i32, [G, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp, vp, vp,
@@ -133,7 +142,8 @@ def exported_symbols():
             "bsi_check_device_status", "bsi_version", "bsi_selfcheck_ranges",
             "bsi_field_adjoint_noalloc", "bsi_set_tile_configs", "bsi_get_tile_config", "bsi_probe_fill",
             "bsi_resample_forward", "bsi_resample_backward_workspace_bytes", "bsi_resample_backward",
-            "bsi_scalar_forward", "bsi_field_forward_variant"]
+            "bsi_scalar_forward", "bsi_field_forward_variant", "bsi_geom_rational_init",
+            "bsi_field_forward_rational"]
 
 
 def bsi_set_tile_configs(configs) -> None:
@@ -342,6 +352,38 @@ def bsi_field_adjoint_batched(grads, spacings, outs=None, workspace=None, stream
                                              _stream(stream, dev))
     _check(st, "bsi_field_adjoint_batched")
     return outs
+
+
+def make_geom_rational(shape, num, den, off):
+    """bsi_geom_rational for a (Z, Y, X) volume; num, den, off in (z, y, x) order."""
+    Z, Y, X = (int(v) for v in shape)
+    arr = lambda a: (ctypes.c_int32 * 3)(*[int(v) for v in tuple(a)[::-1]])   # to (x, y, z)
+    g = BsiGeomRational()
+    st = library().bsi_geom_rational_init(ctypes.byref(g), X, Y, Z, arr(num), arr(den), arr(off))
+    _check(st, "bsi_geom_rational_init")
+    return g
+
+
+def rational_grid_shape(shape, num, den, off):
+    """Stored grid (nz, ny, nx) for spacing num/den and lattice shift off/den voxels
+    per axis ((z, y, x) order): floor(((N - 1) den + off) / num) + 4."""
+    return tuple(((int(N) - 1) * int(d) + int(o)) // int(n) + 4 if int(N) > 0 else 4
+                 for N, n, d, o in zip(shape, num, den, off))
+
+
+def bsi_field_forward_rational(phi, shape, num, den, off=(0, 0, 0), out=None, stream=None):
+    """Eq. 1 with non-integer spacing num/den and lattice shift off/den voxels per
+    axis ((z, y, x) order like ``shape``): FP32 field [Z, Y, X, 3]."""
+    shape = tuple(int(s) for s in shape)
+    _need(phi, "phi", torch.float32, rational_grid_shape(shape, num, den, off) + (3,))
+    if out is None:
+        out = torch.empty(shape + (3,), dtype=torch.float32, device=phi.device)
+    _need(out, "out", torch.float32, shape + (3,))
+    g = make_geom_rational(shape, num, den, off)
+    st = library().bsi_field_forward_rational(ctypes.byref(g), phi.data_ptr(), out.data_ptr(),
+                                              _stream(stream, phi.device))
+    _check(st, "bsi_field_forward_rational")
+    return out
 
 
 VARIANTS = {"separable": 0, "tt": 1, "ttli": 2}

@@ -19,7 +19,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 BUILD = PKG / "_build"
-SOURCES = ["bsi_abi.cu", "bsi_forward.cu", "bsi_adjoint.cu", "bsi_probe.cu", "bsi_resample.cu", "bsi_variants.cu"]
+SOURCES = ["bsi_abi.cu", "bsi_forward.cu", "bsi_adjoint.cu", "bsi_probe.cu", "bsi_resample.cu", "bsi_variants.cu", "bsi_rational.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

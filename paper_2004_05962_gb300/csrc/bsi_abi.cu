@@ -728,6 +728,29 @@ using namespace bsi;
 
 extern "C" {
 
+bsi_status bsi_geom_rational_init(bsi_geom_rational* g, int64_t X, int64_t Y, int64_t Z, const int32_t num[3],
+                                  const int32_t den[3], const int32_t off[3]) {
+    if (!g || !num || !den || !off) return BSI_ERR_NULL;
+    std::memset(g, 0, sizeof *g);
+    g->X = X;
+    g->Y = Y;
+    g->Z = Z;
+    for (int a = 0; a < 3; ++a) {
+        g->num[a] = num[a];
+        g->den[a] = den[a];
+        g->off[a] = off[a];
+    }
+    if (X < 0 || Y < 0 || Z < 0 || X > BSI_MAX_DIM || Y > BSI_MAX_DIM || Z > BSI_MAX_DIM) return BSI_ERR_DIMS;
+    for (int a = 0; a < 3; ++a)
+        if (den[a] < 1 || den[a] > BSI_MAX_RATIONAL_DEN || num[a] < den[a] || num[a] > BSI_MAX_SPACING * den[a] ||
+            off[a] < 0 || off[a] >= num[a])
+            return BSI_ERR_SPACING;
+    g->nx = rational_dim(X, num[0], den[0], off[0]);
+    g->ny = rational_dim(Y, num[1], den[1], off[1]);
+    g->nz = rational_dim(Z, num[2], den[2], off[2]);
+    return BSI_OK;
+}
+
 bsi_status bsi_geom_init(bsi_geom* g, int64_t X, int64_t Y, int64_t Z, int32_t dx, int32_t dy, int32_t dz) {
     if (!g) return BSI_ERR_NULL;
     std::memset(g, 0, sizeof *g);
@@ -838,14 +861,15 @@ bsi_status bsi_get_tile_config(int32_t dx, int32_t dy, int32_t dz, bsi_tile_conf
 
 bsi_status bsi_check_device_status(bsi_stream_t stream, uint32_t* flags) {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    static thread_local unsigned words[4];
+    static thread_local unsigned words[5];
     cudaError_t e = forward_err_read_clear(&words[0], s);
     if (e == cudaSuccess) e = adjoint_err_read_clear(&words[1], s);
     if (e == cudaSuccess) e = resample_err_read_clear(&words[2], s);
     if (e == cudaSuccess) e = variants_err_read_clear(&words[3], s);
+    if (e == cudaSuccess) e = rational_err_read_clear(&words[4], s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e);
-    const uint32_t w = words[0] | words[1] | words[2] | words[3];
+    const uint32_t w = words[0] | words[1] | words[2] | words[3] | words[4];
     if (flags) *flags = w;
     return w ? BSI_ERR_DEVICE_STATUS : BSI_OK;
 }
@@ -897,6 +921,50 @@ bsi_status bsi_field_forward_variant(const bsi_geom* g, const float* phi, float*
     (void)cudaGetLastError();
     const cudaError_t e = launch_forward_tile_variant(b, variant == BSI_VARIANT_TTLI,
                                                       reinterpret_cast<cudaStream_t>(stream), nullptr);
+    return e == cudaSuccess ? BSI_OK : cuda_fail(e);
+}
+
+static bsi_status check_rational(const bsi_geom_rational* g) {
+    if (!g) return BSI_ERR_NULL;
+    if (g->X < 0 || g->Y < 0 || g->Z < 0 || g->X > BSI_MAX_DIM || g->Y > BSI_MAX_DIM || g->Z > BSI_MAX_DIM)
+        return BSI_ERR_DIMS;
+    for (int a = 0; a < 3; ++a) {
+        const int32_t n = g->num[a], d = g->den[a], o = g->off[a];
+        if (d < 1 || d > BSI_MAX_RATIONAL_DEN || n < d || n > BSI_MAX_SPACING * d || o < 0 || o >= n)
+            return BSI_ERR_SPACING;
+    }
+    if (g->nx != rational_dim(g->X, g->num[0], g->den[0], g->off[0]) ||
+        g->ny != rational_dim(g->Y, g->num[1], g->den[1], g->off[1]) ||
+        g->nz != rational_dim(g->Z, g->num[2], g->den[2], g->off[2]))
+        return BSI_ERR_GRID_MISMATCH;
+    if (g->nx > BSI_MAX_RATIONAL_NX) return BSI_ERR_DIMS;
+    return BSI_OK;
+}
+
+bsi_status bsi_field_forward_rational(const bsi_geom_rational* g, const float* phi, float* field,
+                                      bsi_stream_t stream) {
+    bsi_status st = check_rational(g);
+    if (st != BSI_OK) return st;
+    if (g->X == 0 || g->Y == 0 || g->Z == 0) return BSI_OK;
+    if (!phi || !field) return BSI_ERR_NULL;
+    if (misaligned(phi, 4) || misaligned(field, 4)) return BSI_ERR_ALIGN;
+    RatDesc d;
+    std::memset(&d, 0, sizeof d);
+    d.X = (int)g->X;
+    d.Y = (int)g->Y;
+    d.Z = (int)g->Z;
+    for (int a = 0; a < 3; ++a) {
+        d.num[a] = g->num[a];
+        d.den[a] = g->den[a];
+        d.off[a] = g->off[a];
+    }
+    d.nx = (int)g->nx;
+    d.ny = (int)g->ny;
+    d.nz = (int)g->nz;
+    d.phi = phi;
+    d.field = field;
+    (void)cudaGetLastError();
+    const cudaError_t e = launch_forward_rational(d, reinterpret_cast<cudaStream_t>(stream), nullptr);
     return e == cudaSuccess ? BSI_OK : cuda_fail(e);
 }
 

@@ -240,6 +240,22 @@ BSI_HD int tma_default_stages(int stage_bytes) {
 BSI_HD int tma_first_float(const AdjUnit& u, int dx) { return (u.col0 - kHalo) * 3 * dx; }
 BSI_HD int tma_group_of(int f) { return f >= 0 ? f / 4 : -((-f + 3) / 4); }   // floor(f / 4)
 
+// ---------------------------------------------------------------- non-integer spacing
+
+// One volume with spacing num/den and lattice shift off/den per axis (x, y, z).
+struct RatDesc {
+    int X, Y, Z;
+    int num[3], den[3], off[3];
+    int nx, ny, nz;
+    const float* phi;
+    float* field;
+};
+
+// Stored grid points along one axis: floor(((N - 1) den + off) / num) + 4.
+BSI_HD long long rational_dim(long long N, int num, int den, int off) {
+    return N > 0 ? ((N - 1) * den + off) / num + 4 : 4;
+}
+
 constexpr int kMaxWarpsPerCta = 8;
 constexpr int kAdjWarpsMax = 4;   // adjoint partials kernel: 4-warp CTAs (register budget)
 constexpr int kSmemBudget = 200 * 1024;   // dynamic shared memory per CTA we allow

@@ -25,6 +25,11 @@ cudaError_t launch_forward(const Batch<MAXB>& b, bool bf16, bool generic, cudaSt
 cudaError_t launch_forward_tile_variant(const Batch<1>& b, bool lerp, cudaStream_t s, LaunchInfo* info);
 cudaError_t variants_err_read_clear(unsigned* out, cudaStream_t s);
 
+// Non-integer, non-aligned spacing (bsi_rational.cu).
+int rational_warps_per_cta(int nx);
+cudaError_t launch_forward_rational(const RatDesc& d, cudaStream_t s, LaunchInfo* info);
+cudaError_t rational_err_read_clear(unsigned* out, cudaStream_t s);
+
 // Scalar (one-channel) interpolation: Eq. 1 with grid [nz][ny][nx], output [Z][Y][X].
 cudaError_t launch_forward_scalar(const Batch<1>& b, bool bf16, bool generic, cudaStream_t s, LaunchInfo* info);
 

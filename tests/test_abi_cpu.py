@@ -246,3 +246,25 @@ def test_variant_validation_before_cuda(lib):
     assert fv(ctypes.byref(g), fake, fake + 2, 2, None) == 6
     big, _ = _geom(40, 30, 20, 33, 4, 3)
     assert fv(ctypes.byref(big), fake, fake, 2, None) == 3
+
+
+def test_rational_geometry_and_validation_before_cuda(lib):
+    import oracle
+
+    for shape, num, den, off in [((7, 9, 11), (5, 7, 9), (2, 2, 2), (0, 3, 1)), ((300, 512, 512), (47, 47, 47),
+                                                                                 (10, 10, 10), (3, 0, 9))]:
+        g = B.make_geom_rational(shape, num, den, off)
+        assert (g.nz, g.ny, g.nx) == B.rational_grid_shape(shape, num, den, off) == \
+            oracle.rational_grid_shape(shape, num, den, off)
+    fake = 0x7F0000000000  # never dereferenced: validation fails first
+    g = B.make_geom_rational((7, 9, 11), (5, 7, 9), (2, 2, 2), (0, 3, 1))
+    fr = lib.bsi_field_forward_rational
+    assert fr(ctypes.byref(g), None, fake, None) == 1
+    assert fr(ctypes.byref(g), fake + 2, fake, None) == 6
+    g.nx += 1
+    assert fr(ctypes.byref(g), fake, fake, None) == 4
+    for bad in [((1, 1, 1), (2, 1, 1), (0, 0, 0)),          # spacing below 1
+                ((5, 5, 5), (2, 2, 2), (0, 5, 0)),          # shift of a whole cell
+                ((5, 5, 5), (2000, 2, 2), (0, 0, 0))]:      # denominator beyond the limit
+        with pytest.raises(B.BsiError):
+            B.make_geom_rational((7, 9, 11), *bad)
