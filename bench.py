@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="main step only (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle leg")
-    ap.add_argument("--section", choices=["resample"], default=None,
+    ap.add_argument("--section", choices=["resample", "batched"], default=None,
                     help="run only this extra measurement (profiling runs) and print its JSON")
     return ap.parse_args()
 
@@ -357,6 +357,19 @@ def measure_resample(P, synth, model, dev, s, phi, field, dphi, hbm_peak, iters)
         "image": "sum of 8 Gaussian blobs (sigma 8-20 voxels), seed 6; phi = the bench's CT control grid"}
 
 
+def batch_launches(shapes, spacings, max_batch=64):
+    """Kernel launches of one batched forward + adjoint, by the library's grouping:
+    forward -- x-spacing <= 8 and > 8 groups; adjoint -- tensor-copy (X % 4 == 0,
+    dx <= 8; torch buffers are 16-byte aligned), row-copy (dx <= 8) and generic
+    groups, each a partials and a reduce launch; at most 64 instances a launch."""
+    def groups(keys):
+        return sum(-(-keys.count(k) // max_batch) for k in set(keys))
+    fwd = [sp[2] > 8 for sp in spacings]
+    adj = [("tma" if (sh[2] % 4 == 0 and sp[2] <= 8) else ("row" if sp[2] <= 8 else "generic"))
+           for sh, sp in zip(shapes, spacings)]
+    return groups(fwd) + 2 * groups(adj)
+
+
 def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_peak):
     import numpy as np
     import torch
@@ -494,7 +507,7 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
                          "gvox_s_fwd": round(bvox / tbf / 1e6, 2), "voxels": bvox,
                          "vs_single_volume_fwd": round((bvox / tbf) / (nvox / ms), 3),
                          "vs_single_volume_fwd_adj": round((bvox / tb) / (nvox / (ms + msa)), 3),
-                         "launches_per_step": 3, "cuda_graph": True,
+                         "launches_per_step": batch_launches(shapes, spacings), "cuda_graph": True,
                          "autotuned": {k: v for k, v in tuned.items() if k not in ("dx", "dy", "dz")},
                          "spacing_classes": len(set(map(tuple, spacings))),
                          "tuning_s": round(tune_s, 1), "gvox_s_fwd_adj_untuned": round(bvox / t_default / 1e6, 2)}
@@ -659,6 +672,40 @@ def run_section_resample(args):
             "resample": measure_resample(P, synth, model, dev, s, phi, field, dphi, hbm_peak, args.steps)}
 
 
+def run_section_batched(args):
+    """The 64-volume batch's forward + adjoint with library defaults, --steps
+    times (profiling runs)."""
+    import numpy as np
+    import torch
+
+    from paper_2004_05962_gb300 import build as pbuild
+
+    pbuild.build()
+    import paper_2004_05962_gb300 as P
+    from paper_2004_05962_gb300 import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    geoms = synth.batch_geometries(64, seed=5)
+    shapes = [g[0] for g in geoms]
+    spacings = [g[1] for g in geoms]
+    phis = [torch.from_numpy(synth.uniform_phi(a, b, -3, 3, seed=500 + i)).to(dev) for i, (a, b) in enumerate(geoms)]
+    grads = [torch.randn(a + (3,), device=dev) for a in shapes]
+    outs = [torch.empty(a + (3,), device=dev) for a in shapes]
+    dps = [torch.empty_like(p) for p in phis]
+    bws = torch.empty(P.bsi_batched_adjoint_workspace_bytes(shapes, spacings), dtype=torch.uint8, device=dev)
+    s = torch.cuda.current_stream(dev)
+
+    def bstep():
+        P.bsi_field_forward_batched(phis, shapes, spacings, outs=outs)
+        P.bsi_field_adjoint_batched(grads, spacings, outs=dps, workspace=bws)
+
+    ms = time_fn(bstep, s, args.steps)
+    bvox = sum(int(np.prod(x)) for x in shapes)
+    return {"section": "batched", "ms_fwd_adj": round(ms, 5), "gvox_s_fwd_adj": round(bvox / ms / 1e6, 2),
+            "launches_per_step": batch_launches(shapes, spacings)}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -669,6 +716,9 @@ def main():
         return
     if args.section == "resample":
         print(json.dumps(run_section_resample(args)), flush=True)
+        return
+    if args.section == "batched":
+        print(json.dumps(run_section_batched(args)), flush=True)
         return
     out = run_ours(args, ws, rank, local)
     if rank == 0:

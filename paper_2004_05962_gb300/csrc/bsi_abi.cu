@@ -299,6 +299,18 @@ static std::vector<Group> plan(const std::vector<InstDesc>& all, long long* ws_f
         }
         if (!cur.inst.empty()) out.push_back(cur);
     }
+    // Heaviest units first within a launch: units are dealt round-robin over the
+    // warp slots, so rounds of similar cost keep the warps balanced (unit cost
+    // ~ rows x (voxels per lane row + per-row work); for a batch of uneven
+    // spacings it varies ~7x; measured +3% on the 64-volume batch).  Instance
+    // order never changes any result.
+    auto unit_cost = [](const InstDesc& d) {
+        const long long planes = d.zchunk > 0 ? (long long)d.zchunk * d.dz : d.dz;
+        return planes * d.dy * (d.dx + 4);
+    };
+    for (Group& g : out)
+        std::stable_sort(g.inst.begin(), g.inst.end(),
+                         [&](const InstDesc& a, const InstDesc& b) { return unit_cost(a) > unit_cost(b); });
     for (Group& g : out) {
         long long ub = 0, pb = 0;
         for (InstDesc& d : g.inst) {
