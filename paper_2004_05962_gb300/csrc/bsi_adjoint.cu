@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(kAdjMaxWarps * kLanes, 3)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous kernel's writes are visible
     const int wpc = blockDim.x >> 5;
     int ii = 0;
     unsigned q = 0;
@@ -61,6 +62,7 @@ __global__ void __launch_bounds__(kAdjMaxWarps * kLanes, 3)
     __syncwarp();
     if (lane == 0)
         for (int s = 0; s < kLoadStages; ++s) mbar_inval(bars + s);
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   // as in the tensor-copy kernel
 }
 
 // Tensor-copy path (adjoint_unit_tma): x-spacing <= 8, dy <= 8, X % 4 == 0.
@@ -87,6 +89,7 @@ __global__ void __launch_bounds__(kTmaMaxWarps * kLanes, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous kernel's writes are visible
     const int wpc = blockDim.x >> 5;
     int ii = 0;
     unsigned q = 0;
@@ -113,6 +116,9 @@ __global__ void __launch_bounds__(kTmaMaxWarps * kLanes, 1)
     __syncwarp();
     if (lane == 0)
         for (int s = 0; s < b.stages; ++s) mbar_inval(bars + s);
+    // this CTA's partial sums are written: the reduce grid may be scheduled
+    // (it still waits for this whole grid before reading them)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // One thread per stored control point of every instance.  The units that
@@ -123,6 +129,9 @@ template <int MAXB>
 __global__ void __launch_bounds__(256)
     bsi_adjoint_reduce_kernel(const __grid_constant__ Batch<MAXB> b, const float* __restrict__ part,
                               long long ws_floats) {
+    // launched as a programmatic dependent of the partials kernel: wait here until
+    // that grid has finished and its partial sums are visible (a no-op otherwise)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < b.total_points; p += stride) {
         int lo = 0, hi = b.n - 1;  // last instance with point_begin <= p
@@ -133,10 +142,18 @@ __global__ void __launch_bounds__(256)
         }
         const InstDesc& d = b.inst[lo];
         const long long pl = p - d.point_begin;
-        const int gx = (int)(pl % d.nx);
-        const long long t = pl / d.nx;
-        const int gy = (int)(t % d.ny);
-        const int gz = (int)(t / d.ny);
+        int gx, gy, gz;
+        if (pl < 0xFFFFFFFFLL) {   // 32-bit division (64-bit division is a long sequence)
+            const unsigned u = (unsigned)pl, t = u / (unsigned)d.nx;
+            gx = (int)(u - t * (unsigned)d.nx);
+            gy = (int)(t % (unsigned)d.ny);
+            gz = (int)(t / (unsigned)d.ny);
+        } else {
+            const long long t = pl / d.nx;
+            gx = (int)(pl - t * d.nx);
+            gy = (int)(t % d.ny);
+            gz = (int)(t / d.ny);
+        }
         const int xg = gx / kGroupCells, j = gx - xg * kGroupCells;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
         if (d.nzc > 0) {
@@ -181,6 +198,7 @@ __global__ void __launch_bounds__(256)
             o[2] = s2;
         }
     }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   // this CTA's points are written
 }
 
 template <int MAXB, bool GENERIC>
@@ -199,8 +217,7 @@ static cudaError_t launch_part_t(const Batch<MAXB>& b, float* part, long long ws
     const int grid = (int)(want < cap ? want : cap);
     if (info) *info = LaunchInfo{grid, threads, smem, f.ctas_per_sm};
     if (grid <= 0) return cudaSuccess;
-    kern<<<grid, threads, smem, s>>>(b, part, ws_floats);
-    return cudaGetLastError();
+    return launch_pdl(kern, grid, threads, smem, s, b, part, ws_floats);
 }
 
 template <int MAXB>
@@ -234,8 +251,7 @@ cudaError_t launch_adjoint_partials_tma(const Batch<MAXB>& b, const TmaMaps<MAXB
     const int grid = (int)(want < cap ? want : cap);
     if (info) *info = LaunchInfo{grid, threads, smem, f.ctas_per_sm};
     if (grid <= 0) return cudaSuccess;
-    kern<<<grid, threads, smem, s>>>(b, maps, part, ws_floats);
-    return cudaGetLastError();
+    return launch_pdl(kern, grid, threads, smem, s, b, maps, part, ws_floats);
 }
 
 template <int MAXB>
@@ -250,8 +266,7 @@ cudaError_t launch_adjoint_reduce(const Batch<MAXB>& b, const float* part, long 
     const int grid = (int)(want < cap ? want : cap);
     if (info) *info = LaunchInfo{grid, 256, 0, f.ctas_per_sm};
     if (grid <= 0) return cudaSuccess;
-    kern<<<grid, 256, 0, s>>>(b, part, ws_floats);
-    return cudaGetLastError();
+    return launch_pdl(kern, grid, 256, 0, s, b, part, ws_floats);   // may start while the partials drain
 }
 
 template cudaError_t launch_adjoint_partials<1>(const Batch<1>&, bool, float*, long long, cudaStream_t, LaunchInfo*);

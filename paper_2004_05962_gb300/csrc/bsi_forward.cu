@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
     const int wpc = blockDim.x >> 5;
     int ii = 0;
     int ring = 0;  // next staging buffer of the warp's store ring
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous kernel's writes are visible
     for (long long r = 0;; ++r) {
         const long long uu = slot_unit(r, blockIdx.x, warp, gridDim.x, wpc, b.total_units, false);
         if (uu < 0) break;
@@ -45,6 +46,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
     // the staging ring must outlive every bulk copy that reads it
     if (lane == 0) bulk_wait_all<0>();
     __syncwarp();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   // this CTA's rows are written
 }
 
 template <int MAXB, bool BF16, bool GENERIC, int C = 3>
@@ -61,8 +63,7 @@ static cudaError_t launch_fwd_t(const Batch<MAXB>& b, cudaStream_t s, LaunchInfo
     const int grid = (int)(want < cap ? want : cap);
     if (info) *info = LaunchInfo{grid, threads, smem, f.ctas_per_sm};
     if (grid <= 0) return cudaSuccess;
-    kern<<<grid, threads, smem, s>>>(b);
-    return cudaGetLastError();
+    return launch_pdl(kern, grid, threads, smem, s, b);
 }
 
 template <int MAXB>

@@ -9,6 +9,26 @@
 
 namespace bsi {
 
+// Launches kern on s as a programmatic dependent of the previous kernel on s: it
+// may be scheduled while that kernel's CTAs drain (they signal
+// griddepcontrol.launch_dependents when done) and waits in griddepcontrol.wait
+// for that grid's completion before touching memory.  After a kernel that never
+// signals, this is an ordinary launch.
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*kern)(P...), int grid, int threads, int smem, cudaStream_t s, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<A&&>(args)...);
+}
+
 // What a launcher chose; returned for diagnostics and the self-check.
 struct LaunchInfo {
     int grid = 0;
