@@ -333,6 +333,17 @@ bsi_status bsi_resample_backward(const bsi_geom* g, const float* phi, const floa
                                  int64_t fY, int64_t fZ, const float* grad_warped, float* grad_phi,
                                  void* workspace, size_t workspace_bytes, bsi_stream_t stream);
 
+/* Failure-detection self-test, no counterpart in the paper: enqueues one warp
+ * that waits for a bulk copy that never comes -- it arms an mbarrier for 16
+ * bytes and issues no copy -- with the same bounded wait the kernels use on
+ * their copies (at most about 2 s).  When the wait gives up, the warp records
+ * BSI_DEVICE_FLAG_TIMEOUT in the device status word, as a lost copy in a
+ * kernel would, and returns: no fault, no trap, the context stays usable.
+ * Read the result with bsi_check_device_status.  BSI_ERR_CUDA if the launch
+ * fails. */
+#define BSI_DEVICE_FLAG_TIMEOUT 128u
+bsi_status bsi_selftest_lost_copy(bsi_stream_t stream);
+
 /* Measurement utility, no counterpart in the paper: fills `bytes` bytes at
  * device address dst with the 32-bit pattern `value`, through the forward
  * kernel's store path (TMA bulk copies from shared memory, 16 KB each, from

@@ -24,6 +24,7 @@ from .bsi import (  # noqa: F401
     bsi_resample_forward,
     bsi_scalar_forward,
     bsi_selfcheck_ranges,
+    bsi_selftest_lost_copy,
     bsi_set_tile_configs,
     bsi_tile_configs,
     grid_shape,

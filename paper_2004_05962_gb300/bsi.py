@@ -117,6 +117,7 @@ def library(checked: bool | None = None) -> ctypes.CDLL:
         "bsi_get_tile_config": (i32, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.POINTER(BsiTileConfig)]),
         "bsi_probe_fill": (i32, [vp, sz, ctypes.c_uint32, vp]),
+        "bsi_selftest_lost_copy": (i32, [vp]),
         "bsi_scalar_forward": (i32, [G, vp, vp, i32, vp]),
         "bsi_field_forward_variant": (i32, [G, vp, vp, ctypes.c_int32, vp]),
         "bsi_geom_rational_init": (i32, [ctypes.POINTER(BsiGeomRational), ctypes.c_int64, ctypes.c_int64,
@@ -143,7 +144,7 @@ def exported_symbols():
             "bsi_field_adjoint_noalloc", "bsi_set_tile_configs", "bsi_get_tile_config", "bsi_probe_fill",
             "bsi_resample_forward", "bsi_resample_backward_workspace_bytes", "bsi_resample_backward",
             "bsi_scalar_forward", "bsi_field_forward_variant", "bsi_geom_rational_init",
-            "bsi_field_forward_rational"]
+            "bsi_field_forward_rational", "bsi_selftest_lost_copy"]
 
 
 def bsi_set_tile_configs(configs) -> None:
@@ -478,6 +479,17 @@ def bsi_probe_fill(buf: torch.Tensor, value: int = 0, stream=None) -> None:
     st = library().bsi_probe_fill(buf.data_ptr(), buf.numel() * buf.element_size(), value & 0xFFFFFFFF,
                                   _stream(stream, buf.device))
     _check(st, "bsi_probe_fill")
+
+
+DEVICE_FLAG_TIMEOUT = 128
+
+
+def bsi_selftest_lost_copy(stream=None, device=None) -> None:
+    """Enqueues the failure-detection self-test: a wait for a copy that never
+    comes runs out (<= ~2 s) and records DEVICE_FLAG_TIMEOUT; read it with
+    bsi_check_device_status."""
+    st = library().bsi_selftest_lost_copy(_stream(stream, device))
+    _check(st, "bsi_selftest_lost_copy")
 
 
 def bsi_check_device_status(stream=None, device=None) -> int:

@@ -1023,6 +1023,12 @@ bsi_status bsi_resample_backward(const bsi_geom* g, const float* phi, const floa
     return adjoint_impl(&in, 1, static_cast<unsigned char*>(workspace) + goff, workspace_bytes - goff, s);
 }
 
+bsi_status bsi_selftest_lost_copy(bsi_stream_t stream) {
+    (void)cudaGetLastError();
+    const cudaError_t e = launch_selftest_lost_copy(reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? BSI_OK : cuda_fail(e);
+}
+
 int bsi_version(void) { return 100; }
 
 // Host-only: plans the launches of a batched call exactly as the entry points

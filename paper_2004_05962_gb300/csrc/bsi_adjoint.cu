@@ -280,6 +280,29 @@ template cudaError_t launch_adjoint_reduce<1>(const Batch<1>&, const float*, lon
 template cudaError_t launch_adjoint_reduce<kMaxBatch>(const Batch<kMaxBatch>&, const float*, long long,
                                                        cudaStream_t, LaunchInfo*);
 
+// Failure-detection self-test: one warp arms an mbarrier for 16 bytes that no
+// copy will deliver and waits with the kernels' own bounded wait; when it gives
+// up it records kErrTimeout, exactly as a lost bulk copy would, and returns.
+// Nothing is ever in flight on the barrier, so invalidating it is legal.
+__global__ void __launch_bounds__(32) bsi_selftest_lost_copy_kernel() {
+    __shared__ __align__(8) uint64_t bar;
+    const int lane = threadIdx.x;
+    if (lane == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_arrive_expect_tx(&bar, 16);   // the arrival is there; the 16 bytes never come
+    }
+    __syncwarp();
+    if (!mbar_wait_bounded(&bar, 0) && lane == 0) atomicOr(&g_err, kErrTimeout);
+    __syncwarp();
+    if (lane == 0) mbar_inval(&bar);
+}
+
+cudaError_t launch_selftest_lost_copy(cudaStream_t s) {
+    bsi_selftest_lost_copy_kernel<<<1, 32, 0, s>>>();
+    return cudaGetLastError();
+}
+
 cudaError_t adjoint_err_read_clear(unsigned* out, cudaStream_t s) {
     cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_err, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return e;

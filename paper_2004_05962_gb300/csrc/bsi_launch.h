@@ -80,6 +80,9 @@ cudaError_t launch_adjoint_reduce(const Batch<MAXB>& b, const float* part, long 
 cudaError_t launch_resample(const Batch<1>& b, bool grad, bool generic, cudaStream_t s, LaunchInfo* info);
 cudaError_t resample_err_read_clear(unsigned* out, cudaStream_t s);
 
+// Failure-detection self-test (a wait that runs out; see bsi_selftest_lost_copy).
+cudaError_t launch_selftest_lost_copy(cudaStream_t s);
+
 // Reads and clears the kernel error word of each translation unit (enqueued
 // on s; the caller synchronises before looking at *out).
 cudaError_t forward_err_read_clear(unsigned* out, cudaStream_t s);
