@@ -20,6 +20,8 @@ CASES = [
     ((8, 9, 100), (5, 5, 5), (1, 1, 1), (0, 0, 0)),            # integer spacing on this path
     ((10, 10, 33), (640, 13, 23), (10, 5, 7), (639, 4, 22)),   # spacing 64; shift near a full cell
     ((1, 1, 1), (3, 3, 3), (2, 2, 2), (1, 1, 1)),
+    ((3, 5, 1100), (2, 3, 1), (1, 2, 1), (1, 1, 0)),          # nx = 1103: the row-per-warp kernel
+    ((40, 37, 30), (7, 9, 11), (3, 4, 5), (2, 5, 10)),         # several 16-row runs per plane
 ]
 
 
