@@ -57,9 +57,11 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.bsi_oracle_resample.argtypes = geom + [vp, i32, vp, i32, i64, i64, i64, vp, i32]
     lib.bsi_oracle_resample_grad.argtypes = geom + [vp, i32, vp, i32, i64, i64, i64, vp, i32, vp, i32]
     lib.bsi_oracle_forward_rational.argtypes = [i64, i64, i64, vp, vp, vp, vp, i32, vp]
+    lib.bsi_oracle_resample_points.argtypes = geom + [vp, i32, vp, i32, i64, i64, i64, vp, i64, vp, vp]
+    lib.bsi_oracle_forward_rational_points.argtypes = [i64, i64, i64, vp, vp, vp, vp, i32, vp, i64, vp]
     for f in ("bsi_oracle_forward", "bsi_oracle_forward_points", "bsi_oracle_adjoint",
               "bsi_oracle_adjoint_points", "bsi_oracle_resample", "bsi_oracle_resample_grad",
-              "bsi_oracle_forward_rational"):
+              "bsi_oracle_forward_rational", "bsi_oracle_resample_points", "bsi_oracle_forward_rational_points"):
         getattr(lib, f).restype = i32
     return lib
 
@@ -182,6 +184,41 @@ def forward_rational(phi, shape, num, den, off, lib=None) -> np.ndarray:
     if rc:
         raise OracleError("bsi_oracle_forward_rational: bad arguments")
     return out
+
+
+def forward_rational_points(phi, shape, num, den, off, xyz, lib=None) -> np.ndarray:
+    """forward_rational at voxels ``xyz`` [n, 3] given as (x, y, z); returns [n, 3]."""
+    lib = lib or load()
+    Z, Y, X = (int(s) for s in shape)
+    assert phi.shape == rational_grid_shape(shape, num, den, off) + (3,)
+    p, f32 = _in(phi)
+    to_xyz = lambda a: np.ascontiguousarray(np.array(a, np.int64)[::-1])
+    n3, d3, o3 = to_xyz(num), to_xyz(den), to_xyz(off)
+    q = np.ascontiguousarray(xyz, dtype=np.int64).reshape(-1, 3)
+    out = np.empty((q.shape[0], 3), np.float64)
+    rc = lib.bsi_oracle_forward_rational_points(X, Y, Z, n3.ctypes.data, d3.ctypes.data, o3.ctypes.data,
+                                                p.ctypes.data, f32, q.ctypes.data, q.shape[0], out.ctypes.data)
+    if rc:
+        raise OracleError("bsi_oracle_forward_rational_points: bad arguments")
+    return out
+
+
+def resample_points(phi, shape, spacing, image, xyz, lib=None):
+    """resample at voxels ``xyz`` [n, 3] (x, y, z): (values [n], interpolant
+    gradients [n, 3]) in FP64."""
+    lib = lib or load()
+    assert phi.shape == grid_shape(shape, spacing) + (3,)
+    p, f32 = _in(phi)
+    im, if32 = _in(image)
+    fZ, fY, fX = im.shape
+    q = np.ascontiguousarray(xyz, dtype=np.int64).reshape(-1, 3)
+    val = np.empty(q.shape[0], np.float64)
+    grad = np.empty((q.shape[0], 3), np.float64)
+    rc = lib.bsi_oracle_resample_points(*_geom(shape, spacing), p.ctypes.data, f32, im.ctypes.data, if32, fX, fY, fZ,
+                                        q.ctypes.data, q.shape[0], val.ctypes.data, grad.ctypes.data)
+    if rc:
+        raise OracleError("bsi_oracle_resample_points: bad arguments")
+    return val, grad
 
 
 def resample(phi, shape, spacing, image, nthreads: int = 0, lib=None) -> np.ndarray:

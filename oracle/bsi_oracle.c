@@ -587,3 +587,62 @@ int bsi_oracle_forward_rational(int64_t X, int64_t Y, int64_t Z, const int64_t n
             }
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Point-wise versions of the resampling and the non-integer spacing, for     */
+/* checking full-size results on sampled voxels.                             */
+/* ------------------------------------------------------------------------- */
+int bsi_oracle_resample_points(int64_t X, int64_t Y, int64_t Z, int dx, int dy, int dz, const void* phi,
+                               int in_f32, const void* F, int f_f32, int64_t fX, int64_t fY, int64_t fZ,
+                               const int64_t* xyz, int64_t npts, double* value, double* grad) {
+    oracle_geom g;
+    if (oracle_make_geom(&g, X, Y, Z, dx, dy, dz)) return -1;
+    if (fX < 0 || fY < 0 || fZ < 0 || npts < 0 || (npts > 0 && (!phi || !xyz || !value)) ||
+        (fX * fY * fZ > 0 && !F))
+        return -1;
+    const oracle_image im = {F, f_f32, fX, fY, fZ};
+    for (int64_t q = 0; q < npts; ++q) {
+        const int64_t x = xyz[3 * q], y = xyz[3 * q + 1], z = xyz[3 * q + 2];
+        if (x < 0 || y < 0 || z < 0 || x >= X || y >= Y || z >= Z) return -1;
+        double T[3];
+        oracle_eval(&g, phi, in_f32, x, y, z, T);
+        value[q] = oracle_trilinear(&im, (double)x + T[0], (double)y + T[1], (double)z + T[2],
+                                    grad ? grad + 3 * q : NULL);
+    }
+    return 0;
+}
+
+int bsi_oracle_forward_rational_points(int64_t X, int64_t Y, int64_t Z, const int64_t num[3],
+                                       const int64_t den[3], const int64_t off[3], const void* phi,
+                                       int in_f32, const int64_t* xyz, int64_t npts, double* out) {
+    if (X < 0 || Y < 0 || Z < 0 || !num || !den || !off || npts < 0 || (npts > 0 && (!phi || !xyz || !out)))
+        return -1;
+    int64_t n[3];
+    const int64_t N[3] = {X, Y, Z};
+    for (int a = 0; a < 3; ++a) {
+        if (num[a] < 1 || den[a] < 1 || off[a] < 0 || off[a] >= num[a]) return -1;
+        n[a] = oracle_rdim(N[a], num[a], den[a], off[a]);
+    }
+    for (int64_t q = 0; q < npts; ++q) {
+        const int64_t x = xyz[3 * q], y = xyz[3 * q + 1], z = xyz[3 * q + 2];
+        if (x < 0 || y < 0 || z < 0 || x >= X || y >= Y || z >= Z) return -1;
+        int64_t fi, fj, fk;
+        double u, v, w, Bu[4], Bv[4], Bw[4];
+        oracle_raxis(x, num[0], den[0], off[0], &fi, &u);
+        oracle_raxis(y, num[1], den[1], off[1], &fj, &v);
+        oracle_raxis(z, num[2], den[2], off[2], &fk, &w);
+        oracle_basis(u, Bu);
+        oracle_basis(v, Bv);
+        oracle_basis(w, Bw);
+        double* o = out + 3 * q;
+        o[0] = o[1] = o[2] = 0.0;
+        for (int l = 0; l < 4; ++l)
+            for (int m = 0; m < 4; ++m)
+                for (int k = 0; k < 4; ++k) {
+                    const double wt = Bu[l] * Bv[m] * Bw[k];
+                    const int64_t idx = (((fk + k) * n[1] + (fj + m)) * n[0] + (fi + l)) * 3;
+                    for (int c = 0; c < 3; ++c) o[c] += wt * oracle_load(phi, in_f32, idx + c);
+                }
+    }
+    return 0;
+}

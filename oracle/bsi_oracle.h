@@ -88,6 +88,18 @@ int bsi_oracle_forward_rational(int64_t X, int64_t Y, int64_t Z, const int64_t n
                                 const int64_t den[3], const int64_t off[3], const void* phi,
                                 int in_f32, double* field);
 
+/* Point-wise forms (for sampled checks of full-size results): the resampled
+ * value (and, if grad is not NULL, the interpolant's gradient, 3 per point) at
+ * npts voxels xyz[3*npts] = (x, y, z); Eq. 1 with non-integer spacing at npts
+ * voxels (out[3*npts]). */
+int bsi_oracle_resample_points(int64_t X, int64_t Y, int64_t Z, int dx, int dy, int dz,
+                               const void* phi, int in_f32, const void* F, int f_f32,
+                               int64_t fX, int64_t fY, int64_t fZ, const int64_t* xyz,
+                               int64_t npts, double* value, double* grad);
+int bsi_oracle_forward_rational_points(int64_t X, int64_t Y, int64_t Z, const int64_t num[3],
+                                       const int64_t den[3], const int64_t off[3], const void* phi,
+                                       int in_f32, const int64_t* xyz, int64_t npts, double* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -515,6 +515,35 @@ def pin_rational_affine(lib):
     return worst, 1e-13 * scale
 
 
+def pin_new_points_match_dense(lib):
+    """The point-wise resampling and non-integer-spacing functions agree with the
+    dense ones (value and interpolant gradient)."""
+    rng = _rng(45)
+    worst = 0.0
+    shape, spacing, fshape = RESAMPLE_CASES[1]
+    F = rng.normal(size=fshape)
+    phi = rng.uniform(-3, 3, oracle.grid_shape(shape, spacing) + (3,))
+    dW = np.ones(shape)
+    W = oracle.resample(phi, shape, spacing, F, lib=lib)
+    G = oracle.resample_grad(phi, shape, spacing, F, dW, lib=lib)
+    pts = synth_points(shape, 60, rng)
+    v, g = oracle.resample_points(phi, shape, spacing, F, pts, lib=lib)
+    worst = max(worst, float(np.max(np.abs(v - W[pts[:, 2], pts[:, 1], pts[:, 0]]))),
+                float(np.max(np.abs(g - G[pts[:, 2], pts[:, 1], pts[:, 0]]))))
+    for shape, num, den, off in RATIONAL_CASES:
+        phi = rng.uniform(-2, 2, oracle.rational_grid_shape(shape, num, den, off) + (3,))
+        T = oracle.forward_rational(phi, shape, num, den, off, lib=lib)
+        pts = synth_points(shape, 40, rng)
+        Tp = oracle.forward_rational_points(phi, shape, num, den, off, pts, lib=lib)
+        worst = max(worst, float(np.max(np.abs(Tp - T[pts[:, 2], pts[:, 1], pts[:, 0]]))))
+    return worst, 1e-12
+
+
+def synth_points(shape, n, rng):
+    Z, Y, X = shape
+    return np.stack([rng.integers(0, X, n), rng.integers(0, Y, n), rng.integers(0, Z, n)], 1).astype(np.int64)
+
+
 ALL_PINS = [
     pin_partition_of_unity,
     pin_affine_reproduction,
@@ -536,6 +565,7 @@ ALL_PINS = [
     pin_rational_brute_force,
     pin_rational_scipy,
     pin_rational_affine,
+    pin_new_points_match_dense,
 ]
 
 
