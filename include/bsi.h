@@ -302,9 +302,13 @@ bsi_status bsi_scalar_forward(const bsi_geom* g, const float* coeff, void* out, 
  * weight 0).
  * ------------------------------------------------------------------------ */
 
+/* Largest floating image, in elements (the kernels index it with 32-bit offsets). */
+#define BSI_MAX_FLOATING_ELEMS 4294967295ull
+
 /* warped[z][y][x] = F~(x + T_x, y + T_y, z + T_z).
  *   g        : reference volume (X, Y, Z) and spacing; phi [nz][ny][nx][3] on it
- *   floating : device, FP32 [fZ][fY][fX], fX, fY, fZ in 1..BSI_MAX_DIM (BSI_ERR_DIMS)
+ *   floating : device, FP32 [fZ][fY][fX], fX, fY, fZ in 1..BSI_MAX_DIM and
+ *              fX * fY * fZ <= BSI_MAX_FLOATING_ELEMS (else BSI_ERR_DIMS)
  *   warped   : device, FP32 [Z][Y][X], fully overwritten
  * Pointers 4-byte aligned (BSI_ERR_ALIGN), non-NULL (BSI_ERR_NULL; phi and
  * warped may be NULL for an empty volume).  One launch on `stream`. */

@@ -698,6 +698,7 @@ static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecke
 
 static bsi_status check_floating(int64_t fX, int64_t fY, int64_t fZ, const float* floating) {
     if (fX < 1 || fY < 1 || fZ < 1 || fX > BSI_MAX_DIM || fY > BSI_MAX_DIM || fZ > BSI_MAX_DIM) return BSI_ERR_DIMS;
+    if (fX * fY > (int64_t)BSI_MAX_FLOATING_ELEMS / fZ) return BSI_ERR_DIMS;   // 32-bit element offsets
     if (!floating) return BSI_ERR_NULL;
     if (misaligned(floating, 4)) return BSI_ERR_ALIGN;
     return BSI_OK;

@@ -209,6 +209,8 @@ def test_resample_validation_before_cuda(lib):
     g, _ = _geom(40, 30, 20, 5, 4, 3)
     rf = lib.bsi_resample_forward
     assert rf(ctypes.byref(g), fake, fake, 0, 30, 20, fake, None) == 2          # empty floating image
+    assert rf(ctypes.byref(g), fake, fake, 1 << 20, 1 << 12, 1, fake, None) == 2   # 2^32 elements: too many
+    assert rf(ctypes.byref(g), fake, None, 1 << 20, (1 << 12) - 1, 1, fake, None) == 1   # 2^32 - 2^20: admitted
     assert rf(ctypes.byref(g), fake, None, 40, 30, 20, fake, None) == 1         # floating NULL
     assert rf(ctypes.byref(g), fake, fake + 2, 40, 30, 20, fake, None) == 6     # floating misaligned
     assert rf(ctypes.byref(g), None, fake, 40, 30, 20, fake, None) == 1
