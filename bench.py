@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="main step only (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle leg")
-    ap.add_argument("--section", choices=["resample", "batched"], default=None,
+    ap.add_argument("--section", choices=["resample", "batched", "rational"], default=None,
                     help="run only this extra measurement (profiling runs) and print its JSON")
     return ap.parse_args()
 
@@ -415,17 +415,7 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
     pv["separable_ms"] = res["components"]["fwd_f32"]["ms"]
     res["paper_tile_variants"] = pv
 
-    # non-integer, non-aligned spacing: 4.7 voxels per axis, lattice shifted by
-    # 0.3 / 0 / 0.9 voxels (z, y, x), on the 512 x 512 x 300 volume
-    rn, rd, ro = (47, 47, 47), (10, 10, 10), (3, 0, 9)
-    rgrid = P.rational_grid_shape(shape, rn, rd, ro)
-    rphi = torch.rand(rgrid + (3,), device=dev) * 6.0 - 3.0
-    ms_r = time_fn(lambda: P.bsi_field_forward_rational(rphi, shape, rn, rd, ro, out=field), s, iters)
-    rb = model.forward_bytes(shape, (5, 5, 5)) - 12 * model.grid_points(shape, (5, 5, 5)) + 12 * rphi.numel() // 3
-    res["rational_forward"] = {"ms": round(ms_r, 5), "gvox_s": round(nvox / ms_r / 1e6, 2),
-                               "gbs": round(rb / ms_r / 1e6, 1), "frac_of_hbm": round(rb / ms_r / 1e6 / hbm_peak, 4),
-                               "workload": "512x512x300, spacing 4.7 voxels, lattice shift (0.3, 0, 0.9) (z, y, x), FP32"}
-    del rphi
+    res["rational_forward"] = measure_rational(P, model, dev, s, shape, field, hbm_peak, iters)
 
     # scalar BSI: a 4x zoom of a 128 x 128 x 75 image (its samples as control
     # points, one border sample below and two above) into the 512 x 512 x 300 volume
@@ -652,6 +642,40 @@ def run_reference(args, ws, rank):
             "gpu_launches": 0}
 
 
+def measure_rational(P, model, dev, s, shape, field, hbm_peak, iters):
+    """Non-integer, non-aligned spacing: 4.7 voxels per axis, lattice shifted by
+    0.3 / 0 / 0.9 voxels (z, y, x), on the 512 x 512 x 300 volume."""
+    import torch
+
+    nvox = shape[0] * shape[1] * shape[2]
+    rn, rd, ro = (47, 47, 47), (10, 10, 10), (3, 0, 9)
+    rgrid = P.rational_grid_shape(shape, rn, rd, ro)
+    rphi = torch.rand(rgrid + (3,), device=dev) * 6.0 - 3.0
+    ms_r = time_fn(lambda: P.bsi_field_forward_rational(rphi, shape, rn, rd, ro, out=field), s, iters)
+    rb = model.forward_bytes(shape, (5, 5, 5)) - 12 * model.grid_points(shape, (5, 5, 5)) + 12 * rphi.numel() // 3
+    return {"ms": round(ms_r, 5), "gvox_s": round(nvox / ms_r / 1e6, 2),
+            "gbs": round(rb / ms_r / 1e6, 1), "frac_of_hbm": round(rb / ms_r / 1e6 / hbm_peak, 4),
+            "workload": "512x512x300, spacing 4.7 voxels, lattice shift (0.3, 0, 0.9) (z, y, x), FP32"}
+
+
+def run_section_rational(args):
+    import torch
+
+    from paper_2004_05962_gb300 import build as pbuild
+
+    pbuild.build()
+    import paper_2004_05962_gb300 as P
+    from paper_2004_05962_gb300 import model
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    s = torch.cuda.current_stream(dev)
+    field = torch.empty(CT_SHAPE + (3,), device=dev)
+    hbm_peak, _ = measured_peaks()
+    return {"section": "rational", "rational_forward": measure_rational(P, model, dev, s, CT_SHAPE, field, hbm_peak,
+                                                                        args.steps)}
+
+
 def run_section_resample(args):
     import torch
 
@@ -719,6 +743,9 @@ def main():
         return
     if args.section == "batched":
         print(json.dumps(run_section_batched(args)), flush=True)
+        return
+    if args.section == "rational":
+        print(json.dumps(run_section_rational(args)), flush=True)
         return
     out = run_ours(args, ws, rank, local)
     if rank == 0:

@@ -5,14 +5,24 @@
 // voxel x: q = x den + off, f = floor(q / num), u = (q - f num) / num, computed
 // in integers exactly, u rounded once to FP32.
 //
-// With a non-integer spacing a control cell holds a varying number of voxels,
-// so the strip-of-tiles decomposition of the integer path does not apply.  One
-// warp per output row (y, z) instead: the lanes first contract the stored grid
-// over z and y into a line of nx columns in shared memory (16 FMAs per column
-// and channel), then walk the row voxel by voxel -- consecutive lanes,
-// consecutive voxels -- with the 4-tap x sum, writing coalesced streaming
-// stores.  Each lane advances its cell and remainder by exact integer steps
-// (32 den = a num + b), so there is no integer division per voxel.
+// Three kernels:
+// - bsi_rational_strip_kernel (x-spacing <= 8 voxels): the integer path's
+//   decomposition with cells of varying width.  A warp takes the voxels of one
+//   z-cell x one y-cell x a strip of 29 x-cells; lane = stored grid column,
+//   whose 4 x 4 control points it contracts over z and y in registers; the
+//   x stage gets the three neighbouring columns by shuffles, and each lane
+//   writes the (floor or ceil of num/den) voxels of its cell into a staging row
+//   that leaves by bulk copy.
+// - bsi_rational_window_kernel (wider x-cells, nx <= 1024): a warp takes a run
+//   of rows of a plane; the lanes contract the grid over z into a ring of four
+//   grid rows and over y into a line of nx columns in shared memory, then walk
+//   the row voxel by voxel (consecutive lanes, consecutive voxels).
+// - bsi_rational_kernel (wider x-cells, nx > 1024): the same walk, one warp per
+//   row, the line built from the grid directly.  Each lane advances its cell
+//   and remainder by exact integer steps (32 den = a num + b), so there is no
+//   integer division per voxel.
+// All three sum in the same order (z, then y, then x; lowest tap first), so
+// they give bit-identical fields.
 #include "bsi_kernels.cuh"
 #include "bsi_launch.h"
 
@@ -104,20 +114,182 @@ __global__ void __launch_bounds__(kRatWarps * 32) bsi_rational_kernel(const __gr
     }
 }
 
+// ---------------------------------------------------------------- strip kernel
+
+constexpr int kRatStripMaxCell = 8;                            // voxels per x-cell (ceil(num/den)) it takes
+constexpr int kRatStripMinCell = 4;                            // x-spacing num/den it takes, at least
+constexpr int kRatStripVox = kGroupCells * kRatStripMaxCell;   // voxels of one staged row segment
+constexpr int kRatStripBuf = 12 * kRatStripVox + 16;           // + the segment's 16-byte phase
+constexpr int kRatStripWarps = 8;
+constexpr int kRatCellMax = 64;   // rows (planes) of a y-cell (z-cell): spacing <= 64
+constexpr int kRatWeightBytes = 2 * kRatCellMax * 16;   // per warp: the unit's y and z weights
+
+// First voxel of cell k on one axis: the least x with x den + off >= k num.
+__device__ __forceinline__ int cell_first(int k, int num, int den, int off) {
+    const long long t = (long long)k * num - off;
+    return t <= 0 ? 0 : (int)((t + den - 1) / den);
+}
+
+// The four weights of voxel x on one axis, given its cell f.
+__device__ __forceinline__ void axis_weights(int x, int f, int num, int den, int off, float B[4]) {
+    const int r = x * den + off - f * num;
+    bspline4(__fdiv_rn((float)r, (float)num), B);
+}
+
+// Units: (z-cell kz, part zp of its planes, y-cell jy, x-strip xs), xs fastest,
+// so neighbouring warps share grid rows in L1.  ncx / ncy / ncz: cells per
+// axis; nsx: strips per row; zsplit: parts per z-cell (more, smaller units when
+// a volume has few cells for the resident warps).
+// TABLE: the four x weights of every voxel tabulated once per CTA (16 bytes
+// per x, after the staging rings); else computed per voxel.  The y and z
+// weights of a unit's rows and planes are computed once per unit, one row
+// (plane) per lane, into the warp's weight buffer (after the table).
+template <bool TABLE>
+__global__ void __launch_bounds__(kRatStripWarps * 32, 2)
+    bsi_rational_strip_kernel(const __grid_constant__ RatDesc d, int ncx, int ncy, int ncz, int nsx, int zsplit) {
+    extern __shared__ __align__(16) unsigned char rstrip[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpc = blockDim.x >> 5;
+    unsigned char* stage = rstrip + (size_t)warp * kStoreStages * kRatStripBuf;
+    float4* xw = reinterpret_cast<float4*>(rstrip + (size_t)wpc * kStoreStages * kRatStripBuf);
+    float4* yw = xw + (TABLE ? d.X : 0) + (size_t)warp * 2 * kRatCellMax;   // the unit's rows, then its planes
+    float4* zw = yw + kRatCellMax;
+    if (TABLE) {
+        for (int x = threadIdx.x; x < d.X; x += blockDim.x) {
+            float B[4];
+            const int f = (x * d.den[0] + d.off[0]) / d.num[0];
+            axis_weights(x, f, d.num[0], d.den[0], d.off[0], B);
+            xw[x] = make_float4(B[0], B[1], B[2], B[3]);
+        }
+        __syncthreads();
+    }
+    int ring = 0;
+    const long long units = (long long)ncz * zsplit * ncy * nsx;
+    for (long long un = (long long)blockIdx.x * wpc + warp; un < units; un += (long long)gridDim.x * wpc) {
+        const int xs = (int)(un % nsx);
+        const long long t = un / nsx;
+        const int jy = (int)(t % ncy);
+        const long long t2 = t / ncy;
+        const int zp = (int)(t2 % zsplit), kz = (int)(t2 / zsplit);
+        const int zc0 = cell_first(kz, d.num[2], d.den[2], d.off[2]);
+        const int zcn = imin(d.Z, cell_first(kz + 1, d.num[2], d.den[2], d.off[2])) - zc0;
+        const int z0 = zc0 + zcn * zp / zsplit, z1 = zc0 + zcn * (zp + 1) / zsplit;   // this part's planes
+        const int y0 = cell_first(jy, d.num[1], d.den[1], d.off[1]);
+        const int y1 = imin(d.Y, cell_first(jy + 1, d.num[1], d.den[1], d.off[1]));
+        __syncwarp();   // the previous unit's weights are read
+        for (int i = lane; i < y1 - y0; i += 32) {
+            float B[4];
+            axis_weights(y0 + i, jy, d.num[1], d.den[1], d.off[1], B);
+            yw[i] = make_float4(B[0], B[1], B[2], B[3]);
+        }
+        for (int i = lane; i < z1 - z0; i += 32) {
+            float B[4];
+            axis_weights(z0 + i, kz, d.num[2], d.den[2], d.off[2], B);
+            zw[i] = make_float4(B[0], B[1], B[2], B[3]);
+        }
+        __syncwarp();
+        // this lane's grid column and (lanes < 29) its cell's voxels [xa, xb)
+        const int c0 = xs * kGroupCells, col = c0 + lane;
+        const int xa = imin(d.X, cell_first(col, d.num[0], d.den[0], d.off[0]));
+        const int xb = (lane < kGroupCells && col < ncx) ? imin(d.X, cell_first(col + 1, d.num[0], d.den[0], d.off[0]))
+                                                         : xa;
+        // the strip's voxels [sx0, sx1) (warp-uniform)
+        const int sx0 = cell_first(c0, d.num[0], d.den[0], d.off[0]);
+        const int sx1 = imin(d.X, cell_first(imin(c0 + kGroupCells, ncx), d.num[0], d.den[0], d.off[0]));
+
+        float ph[4][4][3];
+#pragma unroll
+        for (int n = 0; n < 4; ++n)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                float a = 0.f, b = 0.f, c = 0.f;
+                if (col < d.nx) {
+                    const long long e = (((long long)(kz + n) * d.ny + (jy + m)) * d.nx + col) * 3;
+                    BSI_GUARD(e >= 0 && e + 3 <= 3LL * d.nx * d.ny * d.nz, kErrPhiRead, &g_err) {
+                        const float* p = d.phi + e;
+                        a = __ldg(p);
+                        b = __ldg(p + 1);
+                        c = __ldg(p + 2);
+                    }
+                }
+                ph[n][m][0] = a;
+                ph[n][m][1] = b;
+                ph[n][m][2] = c;
+            }
+
+        for (int z = z0; z < z1; ++z) {
+            const float4 wz = zw[z - z0];
+            const float Bz[4] = {wz.x, wz.y, wz.z, wz.w};
+            float pz[4][3];
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    pz[m][c] = fmaf(Bz[3], ph[3][m][c], fmaf(Bz[2], ph[2][m][c], fmaf(Bz[1], ph[1][m][c], Bz[0] * ph[0][m][c])));
+            for (int y = y0; y < y1; ++y) {
+                const float4 wy = yw[y - y0];
+                const float By[4] = {wy.x, wy.y, wy.z, wy.w};
+                float p0[3], p1[3], p2[3], p3[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    p0[c] = fmaf(By[3], pz[3][c], fmaf(By[2], pz[2][c], fmaf(By[1], pz[1][c], By[0] * pz[0][c])));
+                    p1[c] = __shfl_down_sync(kFull, p0[c], 1);
+                    p2[c] = __shfl_down_sync(kFull, p0[c], 2);
+                    p3[c] = __shfl_down_sync(kFull, p0[c], 3);
+                }
+                unsigned char* g = reinterpret_cast<unsigned char*>(d.field + (((long long)z * d.Y + y) * d.X + sx0) * 3);
+                const int shift = (int)(reinterpret_cast<uintptr_t>(g) & 15);
+                unsigned char* sb = stage + ring * kRatStripBuf + shift;
+                ring = ring + 1 == kStoreStages ? 0 : ring + 1;
+                // (the ring buffer is free: store_row of the previous row waited for it)
+#pragma unroll 2
+                for (int x = xa; x < xb; ++x) {
+                    float B[4];
+                    if (TABLE) {
+                        const float4 w = xw[x];
+                        B[0] = w.x;
+                        B[1] = w.y;
+                        B[2] = w.z;
+                        B[3] = w.w;
+                    } else {
+                        axis_weights(x, col, d.num[0], d.den[0], d.off[0], B);
+                    }
+                    BSI_GUARD(shift + 12 * (x - sx0) + 12 <= kRatStripBuf && x >= sx0, kErrStage, &g_err) {
+                        const uint32_t sv = smem_u32(sb) + 12u * (uint32_t)(x - sx0);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            sts_f32(sv + 4 * c, fmaf(B[3], p3[c], fmaf(B[2], p2[c], fmaf(B[1], p1[c], B[0] * p0[c]))));
+                    }
+                }
+                fence_proxy_async_smem();   // this lane's staging writes before the bulk copy reads them
+                __syncwarp();
+                BSI_GUARD(sx1 > sx0 && shift + 12 * (sx1 - sx0) <= kRatStripBuf, kErrFieldWrite, &g_err) {
+                    store_row<4>(sb, g, shift, 12 * (sx1 - sx0), lane);
+                }
+                __syncwarp();   // lane 0's ring wait precedes every lane's next staging write
+            }
+        }
+    }
+    // the staging ring must outlive every bulk copy that reads it
+    if (lane == 0) bulk_wait_all<0>();
+    __syncwarp();
+}
+
 // Rows per warp of the windowed kernel, and the grid widths it takes (its
 // shared memory per warp: 4 z-contracted grid rows + the line, 60 nx bytes).
 constexpr int kRatRun = 16;
 constexpr int kRatWindowMaxNx = 1024;
 constexpr int kRatTableMaxX = 2048;   // x cells and weights tabulated per CTA up to this width
 
-// A warp takes a run of kRatRun consecutive rows of one voxel plane z.  It keeps
+// A warp takes a run of `run` (<= kRatRun) consecutive rows of one voxel plane z.  It keeps
 // the z-contraction of the four grid rows the current row needs,
 //   P[g'][col] = sum_n Bz[n] phi[fz+n][g'][col]   (g' = fy .. fy+3, a ring of 4),
 // and adds one grid row whenever the row's cell fy advances (spacing >= 1: at
 // most one per row), so each output row's line costs 4 taps from shared memory
 // instead of 16 grid reads.  Same arithmetic per voxel as bsi_rational_kernel.
 template <bool TABLE>
-__global__ void __launch_bounds__(kRatWarps * 32) bsi_rational_window_kernel(const __grid_constant__ RatDesc d) {
+__global__ void __launch_bounds__(kRatWarps * 32) bsi_rational_window_kernel(const __grid_constant__ RatDesc d, int run) {
     extern __shared__ __align__(16) float rwin[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -144,10 +316,10 @@ __global__ void __launch_bounds__(kRatWarps * 32) bsi_rational_window_kernel(con
     const int step_q = 32 * d.den[0];
     const int step_f = step_q / d.num[0], step_r = step_q - step_f * d.num[0];
     const float fnum = (float)d.num[0];
-    const int runs_y = (d.Y + kRatRun - 1) / kRatRun;
+    const int runs_y = (d.Y + run - 1) / run;
     const long long units = (long long)d.Z * runs_y;
     for (long long un = (long long)blockIdx.x * wpc + warp; un < units; un += (long long)gridDim.x * wpc) {
-        const int z = (int)(un / runs_y), ya = (int)(un % runs_y) * kRatRun, yb = imin(ya + kRatRun, d.Y);
+        const int z = (int)(un / runs_y), ya = (int)(un % runs_y) * run, yb = imin(ya + run, d.Y);
         float Bz[4];
         const int fz = axis_cell(z, d.num[2], d.den[2], d.off[2], Bz);
         int have = -1;   // grid rows have-3 .. have are in the ring (slot = row & 3)
@@ -224,6 +396,42 @@ int rational_warps_per_cta(int nx) {
 }
 
 cudaError_t launch_forward_rational(const RatDesc& d, cudaStream_t s, LaunchInfo* info) {
+    // The strip kernel for x-cells of 4 to 8 voxels whose strips are mostly full
+    // (a strip costs the same with few cells as with 29).  Measured on 256- to
+    // 512-voxel rows: 1.2-1.5x faster than the windowed kernel at spacing
+    // 4.3-5; slower at 3.3 (the per-row work of a strip outweighs its voxels)
+    // and at 6.5 on 256 voxels (40 cells in two strips).
+    const int ncx = (int)(((long long)(d.X - 1) * d.den[0] + d.off[0]) / d.num[0]) + 1;
+    const int nsx = (int)cdiv(ncx, kGroupCells);
+    if (d.num[0] >= kRatStripMinCell * d.den[0] && (d.num[0] + d.den[0] - 1) / d.den[0] <= kRatStripMaxCell &&
+        4 * ncx >= 3 * kGroupCells * nsx) {
+        const int ncy = (int)(((long long)(d.Y - 1) * d.den[1] + d.off[1]) / d.num[1]) + 1;
+        const int ncz = (int)(((long long)(d.Z - 1) * d.den[2] + d.off[2]) / d.num[2]) + 1;
+        const bool table = d.X <= kRatTableMaxX;
+        const int ring_bytes = kStoreStages * kRatStripBuf;
+        const int table_bytes = table ? 16 * d.X : 0;
+        int wpc = (kSmemBudget - table_bytes) / (ring_bytes + kRatWeightBytes);
+        wpc = wpc < 1 ? 1 : (wpc > kRatStripWarps ? kRatStripWarps : wpc);
+        const int threads = wpc * 32, smem = wpc * (ring_bytes + kRatWeightBytes) + table_bytes;
+        const void* kern = table ? reinterpret_cast<const void*>(bsi_rational_strip_kernel<true>)
+                                 : reinterpret_cast<const void*>(bsi_rational_strip_kernel<false>);
+        KernelFacts f;
+        cudaError_t e = kernel_facts(kern, threads, smem, &f);
+        if (e != cudaSuccess) return e;
+        // split z-cells while the units are fewer than the resident warps (a short
+        // volume has few cells); smaller units cost more per voxel, so no further
+        const long long slots = (long long)f.sms * f.ctas_per_sm * wpc;
+        int zsplit = 1;
+        while (2 * zsplit <= d.num[2] / d.den[2] && (long long)ncz * zsplit * ncy * nsx < slots) zsplit *= 2;
+        const long long want = cdiv((long long)ncz * zsplit * ncy * nsx, wpc);
+        const long long cap = (long long)f.sms * f.ctas_per_sm;
+        const int grid = (int)(want < cap ? want : cap);
+        if (info) *info = LaunchInfo{grid, threads, smem, f.ctas_per_sm};
+        if (grid <= 0) return cudaSuccess;
+        if (table) bsi_rational_strip_kernel<true><<<grid, threads, smem, s>>>(d, ncx, ncy, ncz, nsx, zsplit);
+        else bsi_rational_strip_kernel<false><<<grid, threads, smem, s>>>(d, ncx, ncy, ncz, nsx, zsplit);
+        return cudaGetLastError();
+    }
     if (d.nx <= kRatWindowMaxNx) {   // the windowed kernel
         const bool table = d.X <= kRatTableMaxX;
         const int table_bytes = table ? 20 * d.X : 0;
@@ -236,13 +444,18 @@ cudaError_t launch_forward_rational(const RatDesc& d, cudaStream_t s, LaunchInfo
         KernelFacts f;
         cudaError_t e = kernel_facts(kern, threads, smem, &f);
         if (e != cudaSuccess) return e;
-        const long long want = cdiv((long long)d.Z * cdiv(d.Y, kRatRun), wpc);
+        // runs of kRatRun rows, shorter while that leaves fewer runs than a quarter
+        // of the resident warps (a short, wide volume has few rows)
+        const long long slots = (long long)f.sms * f.ctas_per_sm * wpc;
+        int run = kRatRun;
+        while (run > 1 && 4 * (long long)d.Z * cdiv(d.Y, run) < slots) run >>= 1;
+        const long long want = cdiv((long long)d.Z * cdiv(d.Y, run), wpc);
         const long long cap = (long long)f.sms * f.ctas_per_sm;
         const int grid = (int)(want < cap ? want : cap);
         if (info) *info = LaunchInfo{grid, threads, smem, f.ctas_per_sm};
         if (grid <= 0) return cudaSuccess;
-        if (table) bsi_rational_window_kernel<true><<<grid, threads, smem, s>>>(d);
-        else bsi_rational_window_kernel<false><<<grid, threads, smem, s>>>(d);
+        if (table) bsi_rational_window_kernel<true><<<grid, threads, smem, s>>>(d, run);
+        else bsi_rational_window_kernel<false><<<grid, threads, smem, s>>>(d, run);
         return cudaGetLastError();
     }
     const int wpc = rational_warps_per_cta(d.nx);

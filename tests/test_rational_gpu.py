@@ -11,17 +11,27 @@ from gpu_util import FWD_TOL, dev
 
 pytestmark = pytest.mark.gpu
 
-# (shape (Z, Y, X), num, den, off), each (z, y, x): spacing num/den, lattice shift off/den
+# (shape (Z, Y, X), num, den, off), each (z, y, x): spacing num/den, lattice shift off/den.
+# x-spacing 4..8 with mostly full 29-cell strips runs the strip kernel (z-cells
+# split into parts when the volume has few cells); other volumes the windowed
+# kernel (nx <= 1024) or the row-per-warp kernel.
 CASES = [
     ((13, 17, 50), (5, 7, 9), (2, 2, 2), (0, 3, 1)),           # 2.5, 3.5, 4.5
     ((12, 20, 64), (4, 3, 10), (3, 1, 3), (2, 0, 7)),          # 1.33, 3, 3.33
     ((9, 11, 40), (1, 9, 7), (1, 4, 5), (0, 8, 6)),            # 1, 2.25, 1.4
     ((20, 16, 70), (47, 47, 47), (10, 10, 10), (3, 0, 9)),     # 4.7 (a CT voxel ratio), shifted
+    ((9, 10, 136), (47, 47, 47), (10, 10, 10), (3, 0, 9)),     # 4.7, one full strip: strip kernel, z-cells split
     ((8, 9, 100), (5, 5, 5), (1, 1, 1), (0, 0, 0)),            # integer spacing on this path
     ((10, 10, 33), (640, 13, 23), (10, 5, 7), (639, 4, 22)),   # spacing 64; shift near a full cell
     ((1, 1, 1), (3, 3, 3), (2, 2, 2), (1, 1, 1)),
     ((3, 5, 1100), (2, 3, 1), (1, 2, 1), (1, 1, 0)),          # nx = 1103: the row-per-warp kernel
     ((40, 37, 30), (7, 9, 11), (3, 4, 5), (2, 5, 10)),         # several 16-row runs per plane
+    ((3, 4, 2500), (5, 5, 47), (2, 2, 10), (1, 0, 7)),         # X > 2048: x weights computed per voxel
+    ((6, 7, 464), (3, 5, 8), (1, 2, 1), (0, 4, 0)),            # x-spacing 8: full 232-voxel segments
+    ((30, 41, 97), (13, 11, 17), (2, 2, 4), (1, 0, 3)),        # 4.25: one strip, several y- and z-cells
+    ((10, 12, 200), (3, 5, 47), (1, 2, 5), (0, 1, 3)),         # 9.4: windowed kernel
+    ((40, 37, 30), (7, 9, 55), (3, 4, 5), (2, 5, 10)),         # 11: windowed, several runs per plane
+    ((2, 3, 10000), (2, 3, 47), (1, 1, 5), (1, 0, 2)),         # nx = 1067: the row-per-warp kernel
 ]
 
 
