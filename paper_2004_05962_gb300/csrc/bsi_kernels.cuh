@@ -216,6 +216,8 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
     const long long plane_pitch = row_pitch * d.Y;       // bytes from plane z to plane z + 1
     unsigned char* gplane =
         static_cast<unsigned char*>(d.field) + ((((long long)z0 * d.Y + y0) * d.X + u.x0) * C) * ES;   // field_elem for C
+    // every row of the unit starts on a 16-byte boundary (x0 is a multiple of DX)
+    const bool direct = C == 1 && (reinterpret_cast<uintptr_t>(d.field) & 15) == 0 && (d.X & 3) == 0;
 
     for (int rz = 0; rz < zn; ++rz, gplane += plane_pitch) {
         const float a0 = c_lut.w[wzb + 4 * rz], a1 = c_lut.w[wzb + 4 * rz + 1];
@@ -240,6 +242,33 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
                 p3[c] = __shfl_down_sync(kFull, p0[c], 3);
             }
 
+            if constexpr (C == 1 && !BF16 && DX == 4) {
+                if (direct) {
+                    // one-channel FP32 rows on 16-byte boundaries at x-spacing 4: a lane's
+                    // tile is one 16-byte vector, so the warp's stores of its tiles are
+                    // contiguous -- no staging, no bulk copy (0.103 -> 0.074 ms for a 4x
+                    // zoom to 512 x 512 x 300; at spacing 8 two vectors per lane leave
+                    // each store instruction half-sector gaps and the bulk copy wins)
+                    BSI_GUARD(rn == 0 || (g - static_cast<unsigned char*>(d.field)) / 4 + xl + rn <=
+                                             (long long)d.X * d.Y * d.Z, kErrFieldWrite, err) {
+                        if (rn > 0) {
+                            float v[DX];
+#pragma unroll
+                            for (int r = 0; r < DX; ++r) {
+                                const int wo = weight_base(DX) + 4 * r;
+                                const float w0 = c_lut.w[wo], w1 = c_lut.w[wo + 1], w2 = c_lut.w[wo + 2],
+                                            w3 = c_lut.w[wo + 3];
+                                v[r] = fmaf(w3, p3[0], fmaf(w2, p2[0], fmaf(w1, p1[0], w0 * p0[0])));
+                            }
+                            float4* o = reinterpret_cast<float4*>(g + 4 * xl);
+#pragma unroll
+                            for (int i = 0; i < DX / 4; ++i)
+                                if (4 * i < rn) __stcs(o + i, make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]));
+                        }
+                    }
+                    continue;
+                }
+            }
             const int shift = (int)(reinterpret_cast<uintptr_t>(g) & 15);
             unsigned char* sb = stage + ring * buf_bytes + shift;
             ring = ring == kStoreStages - 1 ? 0 : ring + 1;

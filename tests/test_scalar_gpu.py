@@ -13,6 +13,7 @@ pytestmark = pytest.mark.gpu
 
 CASES = [
     ((64, 64, 64), (5, 5, 5)),
+    ((14, 21, 236), (3, 5, 4)),     # x-spacing 4, X % 4 == 0: direct 16-byte stores, 3 strips
     ((9, 10, 11), (2, 2, 2)),
     ((13, 7, 40), (3, 2, 3)),
     ((17, 19, 23), (4, 4, 4)),
@@ -57,6 +58,25 @@ def test_scalar_is_channel_of_the_field_bitwise(shape, spacing):
             s = P.bsi_scalar_forward(phit[..., c].contiguous(), shape, spacing, out_dtype=dt)
             torch.cuda.synchronize()
             assert torch.equal(s, field[..., c]), (dt, c)
+
+
+def test_scalar_direct_stores_equal_the_staged_path():
+    """At x-spacing 4 with rows on 16-byte boundaries each lane stores its tile
+    as one 16-byte vector; an output 4 bytes off that boundary takes the staged
+    bulk-copy path.  Both give the same bits."""
+    shape, spacing = (10, 13, 120), (4, 3, 4)
+    rng = np.random.default_rng(41)
+    coeff = torch.from_numpy(rng.uniform(-2, 2, synth.grid_shape(shape, spacing)).astype(np.float32)).to(dev())
+    n = shape[0] * shape[1] * shape[2]
+    buf = torch.empty(n + 4, device=dev())
+    aligned = P.bsi_scalar_forward(coeff, shape, spacing)
+    assert aligned.data_ptr() % 16 == 0
+    off = buf[1:n + 1].view(shape)
+    assert off.data_ptr() % 16 == 4
+    P.bsi_scalar_forward(coeff, shape, spacing, out=off)
+    torch.cuda.synchronize()
+    assert torch.equal(aligned, off)
+    assert P.bsi_check_device_status() == 0
 
 
 def test_scalar_zoom_of_a_smooth_image():
