@@ -144,7 +144,7 @@ __device__ __forceinline__ void axis_weights(int x, int f, int num, int den, int
 // per x, after the staging rings); else computed per voxel.  The y and z
 // weights of a unit's rows and planes are computed once per unit, one row
 // (plane) per lane, into the warp's weight buffer (after the table).
-template <bool TABLE>
+template <bool TABLE, int CMAX>
 __global__ void __launch_bounds__(kRatStripWarps * 32, 2)
     bsi_rational_strip_kernel(const __grid_constant__ RatDesc d, int ncx, int ncy, int ncz, int nsx, int zsplit) {
     extern __shared__ __align__(16) unsigned char rstrip[];
@@ -243,8 +243,11 @@ __global__ void __launch_bounds__(kRatStripWarps * 32, 2)
                 unsigned char* sb = stage + ring * kRatStripBuf + shift;
                 ring = ring + 1 == kStoreStages ? 0 : ring + 1;
                 // (the ring buffer is free: store_row of the previous row waited for it)
-#pragma unroll 2
-                for (int x = xa; x < xb; ++x) {
+                // CMAX = ceil(num / den) >= xb - xa: a fixed, unrolled trip count
+#pragma unroll
+                for (int i = 0; i < CMAX; ++i) {
+                    const int x = xa + i;
+                    if (x >= xb) break;
                     float B[4];
                     if (TABLE) {
                         const float4 w = xw[x];
@@ -413,8 +416,22 @@ cudaError_t launch_forward_rational(const RatDesc& d, cudaStream_t s, LaunchInfo
         int wpc = (kSmemBudget - table_bytes) / (ring_bytes + kRatWeightBytes);
         wpc = wpc < 1 ? 1 : (wpc > kRatStripWarps ? kRatStripWarps : wpc);
         const int threads = wpc * 32, smem = wpc * (ring_bytes + kRatWeightBytes) + table_bytes;
-        const void* kern = table ? reinterpret_cast<const void*>(bsi_rational_strip_kernel<true>)
-                                 : reinterpret_cast<const void*>(bsi_rational_strip_kernel<false>);
+        const int cmax = (d.num[0] + d.den[0] - 1) / d.den[0];   // 4 .. 8
+        const void* kern = nullptr;
+        switch (cmax) {
+#define BSI_RAT_STRIP_KERN(CM)                                                                      \
+    case CM:                                                                                        \
+        kern = table ? reinterpret_cast<const void*>(bsi_rational_strip_kernel<true, CM>)           \
+                     : reinterpret_cast<const void*>(bsi_rational_strip_kernel<false, CM>);         \
+        break;
+            BSI_RAT_STRIP_KERN(4)
+            BSI_RAT_STRIP_KERN(5)
+            BSI_RAT_STRIP_KERN(6)
+            BSI_RAT_STRIP_KERN(7)
+            BSI_RAT_STRIP_KERN(8)
+#undef BSI_RAT_STRIP_KERN
+            default: return cudaErrorInvalidValue;
+        }
         KernelFacts f;
         cudaError_t e = kernel_facts(kern, threads, smem, &f);
         if (e != cudaSuccess) return e;
@@ -428,8 +445,8 @@ cudaError_t launch_forward_rational(const RatDesc& d, cudaStream_t s, LaunchInfo
         const int grid = (int)(want < cap ? want : cap);
         if (info) *info = LaunchInfo{grid, threads, smem, f.ctas_per_sm};
         if (grid <= 0) return cudaSuccess;
-        if (table) bsi_rational_strip_kernel<true><<<grid, threads, smem, s>>>(d, ncx, ncy, ncz, nsx, zsplit);
-        else bsi_rational_strip_kernel<false><<<grid, threads, smem, s>>>(d, ncx, ncy, ncz, nsx, zsplit);
+        void* args[] = {const_cast<RatDesc*>(&d), (void*)&ncx, (void*)&ncy, (void*)&ncz, (void*)&nsx, (void*)&zsplit};
+        return cudaLaunchKernel(kern, dim3(grid), dim3(threads), args, (size_t)smem, s);
         return cudaGetLastError();
     }
     if (d.nx <= kRatWindowMaxNx) {   // the windowed kernel
