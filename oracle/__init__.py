@@ -59,6 +59,8 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.bsi_oracle_forward_rational.argtypes = [i64, i64, i64, vp, vp, vp, vp, i32, vp]
     lib.bsi_oracle_resample_points.argtypes = geom + [vp, i32, vp, i32, i64, i64, i64, vp, i64, vp, vp]
     lib.bsi_oracle_forward_rational_points.argtypes = [i64, i64, i64, vp, vp, vp, vp, i32, vp, i64, vp]
+    lib.bsi_oracle_adjoint_rational.argtypes = [i64, i64, i64, vp, vp, vp, vp, i32, vp]
+    lib.bsi_oracle_adjoint_rational_points.argtypes = [i64, i64, i64, vp, vp, vp, vp, i32, vp, i64, vp]
     for f in ("bsi_oracle_forward", "bsi_oracle_forward_points", "bsi_oracle_adjoint",
               "bsi_oracle_adjoint_points", "bsi_oracle_resample", "bsi_oracle_resample_grad",
               "bsi_oracle_forward_rational", "bsi_oracle_resample_points", "bsi_oracle_forward_rational_points"):
@@ -200,6 +202,38 @@ def forward_rational_points(phi, shape, num, den, off, xyz, lib=None) -> np.ndar
                                                 p.ctypes.data, f32, q.ctypes.data, q.shape[0], out.ctypes.data)
     if rc:
         raise OracleError("bsi_oracle_forward_rational_points: bad arguments")
+    return out
+
+
+def adjoint_rational(grad, num, den, off, lib=None) -> np.ndarray:
+    """Transpose of forward_rational: dphi [nz, ny, nx, 3] (FP64) from grad
+    [Z, Y, X, 3]; num, den, off are (z, y, x)."""
+    lib = lib or load()
+    Z, Y, X = (int(s) for s in grad.shape[:3])
+    g, f32 = _in(grad)
+    to_xyz = lambda a: np.ascontiguousarray(np.array(a, np.int64)[::-1])
+    n3, d3, o3 = to_xyz(num), to_xyz(den), to_xyz(off)
+    out = np.empty(rational_grid_shape((Z, Y, X), num, den, off) + (3,), np.float64)
+    rc = lib.bsi_oracle_adjoint_rational(X, Y, Z, n3.ctypes.data, d3.ctypes.data, o3.ctypes.data, g.ctypes.data,
+                                         f32, out.ctypes.data)
+    if rc:
+        raise OracleError("bsi_oracle_adjoint_rational: bad arguments")
+    return out
+
+
+def adjoint_rational_points(grad, num, den, off, gxyz, lib=None) -> np.ndarray:
+    """adjoint_rational at stored control points ``gxyz`` [n, 3] as (gx, gy, gz)."""
+    lib = lib or load()
+    Z, Y, X = (int(s) for s in grad.shape[:3])
+    g, f32 = _in(grad)
+    to_xyz = lambda a: np.ascontiguousarray(np.array(a, np.int64)[::-1])
+    n3, d3, o3 = to_xyz(num), to_xyz(den), to_xyz(off)
+    q = np.ascontiguousarray(gxyz, dtype=np.int64).reshape(-1, 3)
+    out = np.empty((q.shape[0], 3), np.float64)
+    rc = lib.bsi_oracle_adjoint_rational_points(X, Y, Z, n3.ctypes.data, d3.ctypes.data, o3.ctypes.data,
+                                                g.ctypes.data, f32, q.ctypes.data, q.shape[0], out.ctypes.data)
+    if rc:
+        raise OracleError("bsi_oracle_adjoint_rational_points: bad arguments")
     return out
 
 

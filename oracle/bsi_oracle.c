@@ -588,6 +588,111 @@ int bsi_oracle_forward_rational(int64_t X, int64_t Y, int64_t Z, const int64_t n
     return 0;
 }
 
+/* Transpose of bsi_oracle_forward_rational: every voxel scatters W(x, g) grad[x]
+ * onto its 4 x 4 x 4 stored control points, in voxel order, in FP64. */
+int bsi_oracle_adjoint_rational(int64_t X, int64_t Y, int64_t Z, const int64_t num[3], const int64_t den[3],
+                                const int64_t off[3], const void* grad, int in_f32, double* dphi) {
+    if (X < 0 || Y < 0 || Z < 0 || !num || !den || !off || !dphi || (X * Y * Z > 0 && !grad)) return -1;
+    int64_t n[3];
+    const int64_t N[3] = {X, Y, Z};
+    for (int a = 0; a < 3; ++a) {
+        if (num[a] < 1 || den[a] < 1 || off[a] < 0 || off[a] >= num[a]) return -1;
+        n[a] = oracle_rdim(N[a], num[a], den[a], off[a]);
+    }
+    memset(dphi, 0, (size_t)(n[0] * n[1] * n[2] * 3) * sizeof(double));
+    for (int64_t z = 0; z < Z; ++z)
+        for (int64_t y = 0; y < Y; ++y)
+            for (int64_t x = 0; x < X; ++x) {
+                int64_t fi, fj, fk;
+                double u, v, w, Bu[4], Bv[4], Bw[4], G[3];
+                oracle_raxis(x, num[0], den[0], off[0], &fi, &u);
+                oracle_raxis(y, num[1], den[1], off[1], &fj, &v);
+                oracle_raxis(z, num[2], den[2], off[2], &fk, &w);
+                if (fi < 0 || fj < 0 || fk < 0 || fi + 3 >= n[0] || fj + 3 >= n[1] || fk + 3 >= n[2])
+                    return -1;   /* a neighbourhood outside the grid: the cell arithmetic is wrong */
+                oracle_basis(u, Bu);
+                oracle_basis(v, Bv);
+                oracle_basis(w, Bw);
+                const int64_t vi = ((z * Y + y) * X + x) * 3;
+                for (int c = 0; c < 3; ++c) G[c] = oracle_load(grad, in_f32, vi + c);
+                for (int l = 0; l < 4; ++l)
+                    for (int m = 0; m < 4; ++m)
+                        for (int k = 0; k < 4; ++k) {
+                            const double wt = Bu[l] * Bv[m] * Bw[k];
+#if ORACLE_MUTANT == 13 /* non-integer spacing adjoint: scatters to the mirrored x neighbour */
+                            const int64_t col = fi + (3 - l);
+#else
+                            const int64_t col = fi + l;
+#endif
+                            const int64_t idx = (((fk + k) * n[1] + (fj + m)) * n[0] + col) * 3;
+                            for (int c = 0; c < 3; ++c) dphi[idx + c] += wt * G[c];
+                        }
+            }
+    return 0;
+}
+
+/* The voxels of one stored index g's support on one axis: those whose cell f
+ * has f <= g <= f + 3; their weight is B_{g - f}(u).  Returns the count. */
+static int64_t oracle_rsupport(int64_t g, int64_t N, int64_t num, int64_t den, int64_t off, int64_t* xs,
+                               double* ws) {
+    int64_t cnt = 0;
+    for (int64_t x = 0; x < N; ++x) {
+        int64_t f;
+        double u, B[4];
+        oracle_raxis(x, num, den, off, &f, &u);
+        if (f > g || f + 3 < g) continue;
+        oracle_basis(u, B);
+        xs[cnt] = x;
+        ws[cnt] = B[g - f];
+        ++cnt;
+    }
+    return cnt;
+}
+
+int bsi_oracle_adjoint_rational_points(int64_t X, int64_t Y, int64_t Z, const int64_t num[3],
+                                       const int64_t den[3], const int64_t off[3], const void* grad,
+                                       int in_f32, const int64_t* gxyz, int64_t npts, double* out) {
+    if (X < 0 || Y < 0 || Z < 0 || !num || !den || !off || npts < 0 ||
+        (npts > 0 && (!grad || !gxyz || !out)))
+        return -1;
+    int64_t n[3];
+    const int64_t N[3] = {X, Y, Z};
+    for (int a = 0; a < 3; ++a) {
+        if (num[a] < 1 || den[a] < 1 || off[a] < 0 || off[a] >= num[a]) return -1;
+        n[a] = oracle_rdim(N[a], num[a], den[a], off[a]);
+    }
+    int64_t* xs[3];
+    double* ws[3];
+    for (int a = 0; a < 3; ++a) {
+        xs[a] = (int64_t*)malloc((size_t)(N[a] + 1) * sizeof(int64_t));
+        ws[a] = (double*)malloc((size_t)(N[a] + 1) * sizeof(double));
+    }
+    int rc = 0;
+    for (int64_t q = 0; q < npts && !rc; ++q) {
+        int64_t cnt[3];
+        for (int a = 0; a < 3; ++a) {
+            const int64_t g = gxyz[3 * q + a];
+            if (g < 0 || g >= n[a]) { rc = -1; break; }
+            cnt[a] = oracle_rsupport(g, N[a], num[a], den[a], off[a], xs[a], ws[a]);
+        }
+        if (rc) break;
+        double* o = out + 3 * q;
+        o[0] = o[1] = o[2] = 0.0;
+        for (int64_t c2 = 0; c2 < cnt[2]; ++c2)
+            for (int64_t c1 = 0; c1 < cnt[1]; ++c1)
+                for (int64_t c0 = 0; c0 < cnt[0]; ++c0) {
+                    const double wt = ws[0][c0] * ws[1][c1] * ws[2][c2];
+                    const int64_t vi = ((xs[2][c2] * Y + xs[1][c1]) * X + xs[0][c0]) * 3;
+                    for (int c = 0; c < 3; ++c) o[c] += wt * oracle_load(grad, in_f32, vi + c);
+                }
+    }
+    for (int a = 0; a < 3; ++a) {
+        free(xs[a]);
+        free(ws[a]);
+    }
+    return rc;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Point-wise versions of the resampling and the non-integer spacing, for     */
 /* checking full-size results on sampled voxels.                             */

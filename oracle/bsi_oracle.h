@@ -88,6 +88,18 @@ int bsi_oracle_forward_rational(int64_t X, int64_t Y, int64_t Z, const int64_t n
                                 const int64_t den[3], const int64_t off[3], const void* phi,
                                 int in_f32, double* field);
 
+/* Transpose of bsi_oracle_forward_rational (the gradient with respect to the
+ * grid): dphi[nz][ny][nx][3] = sum over voxels of W(x, g) grad[x], FP64, in
+ * voxel order.  Single-threaded.  The _points form sums, for each of npts
+ * stored control points gxyz[3*npts] = (gx, gy, gz), over the voxels of its
+ * support (out[3*npts]). */
+int bsi_oracle_adjoint_rational(int64_t X, int64_t Y, int64_t Z, const int64_t num[3],
+                                const int64_t den[3], const int64_t off[3], const void* grad,
+                                int in_f32, double* dphi);
+int bsi_oracle_adjoint_rational_points(int64_t X, int64_t Y, int64_t Z, const int64_t num[3],
+                                       const int64_t den[3], const int64_t off[3], const void* grad,
+                                       int in_f32, const int64_t* gxyz, int64_t npts, double* out);
+
 /* Point-wise forms (for sampled checks of full-size results): the resampled
  * value (and, if grad is not NULL, the interpolant's gradient, 3 per point) at
  * npts voxels xyz[3*npts] = (x, y, z); Eq. 1 with non-integer spacing at npts

@@ -18,6 +18,7 @@ MUTANTS = {
     10: "resampling: sign of the z derivative flipped",
     11: "resampling: edge values repeated outside the image",
     12: "non-integer spacing: lattice shift with the wrong sign",
+    13: "non-integer spacing adjoint: scatters to the mirrored x neighbour",
 }
 
 
