@@ -653,8 +653,15 @@ def measure_rational(P, model, dev, s, shape, field, hbm_peak, iters):
     rphi = torch.rand(rgrid + (3,), device=dev) * 6.0 - 3.0
     ms_r = time_fn(lambda: P.bsi_field_forward_rational(rphi, shape, rn, rd, ro, out=field), s, iters)
     rb = model.forward_bytes(shape, (5, 5, 5)) - 12 * model.grid_points(shape, (5, 5, 5)) + 12 * rphi.numel() // 3
+    # its transpose: the field buffer as the voxel gradient, dL/dphi into a grid-shaped buffer
+    rdphi = torch.empty_like(rphi)
+    rws = torch.empty(P.bsi_rational_adjoint_workspace_bytes(shape, rn, rd, ro), dtype=torch.uint8, device=dev)
+    ms_a = time_fn(lambda: P.bsi_field_adjoint_rational(field, rn, rd, ro, out=rdphi, workspace=rws), s, iters)
     return {"ms": round(ms_r, 5), "gvox_s": round(nvox / ms_r / 1e6, 2),
             "gbs": round(rb / ms_r / 1e6, 1), "frac_of_hbm": round(rb / ms_r / 1e6 / hbm_peak, 4),
+            "adjoint_ms": round(ms_a, 5), "adjoint_gvox_s": round(nvox / ms_a / 1e6, 2),
+            "adjoint_gbs": round(rb / ms_a / 1e6, 1), "adjoint_frac_of_hbm": round(rb / ms_a / 1e6 / hbm_peak, 4),
+            "adjoint_workspace_mb": round(rws.numel() / 1e6, 1),
             "workload": "512x512x300, spacing 4.7 voxels, lattice shift (0.3, 0, 0.9) (z, y, x), FP32"}
 
 

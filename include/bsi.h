@@ -253,6 +253,28 @@ bsi_status bsi_geom_rational_init(bsi_geom_rational* g, int64_t X, int64_t Y, in
 bsi_status bsi_field_forward_rational(const bsi_geom_rational* g, const float* phi, float* field,
                                       bsi_stream_t stream);
 
+/* Workspace bytes bsi_field_adjoint_rational needs (partial sums: 6 KB per unit
+ * of one z-cell part x one y-cell x a strip of up to 29 x-cells); 0 for an
+ * invalid or empty geometry. */
+size_t bsi_rational_adjoint_workspace_bytes(const bsi_geom_rational* g);
+
+/* Transpose of bsi_field_forward_rational (the gradient of a loss with respect
+ * to the grid, given grad_field = dL/dfield):
+ *   grad_phi[g] = sum over voxels x of W(x, g) grad_field[x],
+ * W(x, g) the product of the three axes' weights of bsi_field_forward_rational.
+ * Deterministic (fixed summation order, no atomics): per-unit partial sums in
+ * the workspace, then one sum per control point.
+ *   grad_field : device, FP32 [Z][Y][X][3], read only
+ *   grad_phi   : device, FP32 [nz][ny][nx][3], fully overwritten (zeros for an
+ *                empty volume)
+ *   workspace  : device, >= bsi_rational_adjoint_workspace_bytes(g) bytes,
+ *                16-byte aligned; contents on entry ignored
+ * Pointers 4-byte aligned (BSI_ERR_ALIGN); BSI_ERR_WORKSPACE for a missing or
+ * short workspace; geometry checks as bsi_field_forward_rational.  Two
+ * launches on `stream`. */
+bsi_status bsi_field_adjoint_rational(const bsi_geom_rational* g, const float* grad_field, float* grad_phi,
+                                      void* workspace, size_t workspace_bytes, bsi_stream_t stream);
+
 /* The paper's own GPU formulations of Eq. 1, for its accuracy comparison
  * (Sec. 5.3) and as a measured contrast to the separable kernel:
  *   BSI_VARIANT_SEPARABLE  bsi_field_forward's strip kernel (FP32 output)

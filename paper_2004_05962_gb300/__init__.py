@@ -14,7 +14,9 @@ from .bsi import (  # noqa: F401
     bsi_field_adjoint_batched,
     bsi_field_forward,
     bsi_field_forward_batched,
+    bsi_field_adjoint_rational,
     bsi_field_forward_rational,
+    bsi_rational_adjoint_workspace_bytes,
     bsi_field_forward_variant,
     bsi_field_adjoint_noalloc,
     bsi_get_tile_config,
@@ -31,4 +33,4 @@ from .bsi import (  # noqa: F401
     rational_grid_shape,
     library,
 )
-from .autograd import BSIField, BSIResample, field, resample  # noqa: F401
+from .autograd import BSIField, BSIFieldRational, BSIResample, field, field_rational, resample  # noqa: F401

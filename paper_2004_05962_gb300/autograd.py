@@ -9,7 +9,8 @@ from __future__ import annotations
 
 import torch
 
-from .bsi import bsi_field_adjoint, bsi_field_forward, bsi_resample_backward, bsi_resample_forward
+from .bsi import (bsi_field_adjoint, bsi_field_adjoint_rational, bsi_field_forward, bsi_field_forward_rational,
+                  bsi_resample_backward, bsi_resample_forward)
 
 
 class BSIField(torch.autograd.Function):
@@ -30,6 +31,31 @@ def field(phi: torch.Tensor, shape, spacing) -> torch.Tensor:
     """Dense displacement field [Z, Y, X, 3] from control grid phi [nz, ny, nx, 3]
     (shape = (Z, Y, X), spacing = (dz, dy, dx) voxels), differentiable in phi."""
     return BSIField.apply(phi, tuple(int(s) for s in shape), tuple(int(s) for s in spacing))
+
+
+class BSIFieldRational(torch.autograd.Function):
+    """Eq. 1 on a grid of non-integer spacing num/den with lattice shift off/den
+    per axis: forward ``bsi_field_forward_rational``, backward its transpose
+    ``bsi_field_adjoint_rational``."""
+
+    @staticmethod
+    def forward(ctx, phi, shape, num, den, off):
+        ctx.rat = (tuple(int(v) for v in num), tuple(int(v) for v in den), tuple(int(v) for v in off))
+        return bsi_field_forward_rational(phi.contiguous(), shape, *ctx.rat)
+
+    @staticmethod
+    def backward(ctx, grad_field):
+        g = grad_field.contiguous()
+        if g.dtype != torch.float32:
+            g = g.float()
+        return bsi_field_adjoint_rational(g, *ctx.rat), None, None, None, None
+
+
+def field_rational(phi: torch.Tensor, shape, num, den, off=(0, 0, 0)) -> torch.Tensor:
+    """Dense displacement field [Z, Y, X, 3] from a control grid of spacing
+    num/den voxels and lattice shift off/den voxels per axis ((z, y, x) order
+    like ``shape``), differentiable in phi."""
+    return BSIFieldRational.apply(phi, tuple(int(s) for s in shape), num, den, off)
 
 
 class BSIResample(torch.autograd.Function):

@@ -123,6 +123,8 @@ def library(checked: bool | None = None) -> ctypes.CDLL:
         "bsi_geom_rational_init": (i32, [ctypes.POINTER(BsiGeomRational), ctypes.c_int64, ctypes.c_int64,
                                          ctypes.c_int64, vp, vp, vp]),
         "bsi_field_forward_rational": (i32, [ctypes.POINTER(BsiGeomRational), vp, vp, vp]),
+        "bsi_rational_adjoint_workspace_bytes": (sz, [ctypes.POINTER(BsiGeomRational)]),
+        "bsi_field_adjoint_rational": (i32, [ctypes.POINTER(BsiGeomRational), vp, vp, vp, sz, vp]),
         "bsi_resample_forward": (i32, [G, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp, vp]),
         "bsi_resample_backward_workspace_bytes": (sz, [G]),
         "bsi_resample_backward": (i32, [G, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp, vp, vp,
@@ -144,7 +146,8 @@ def exported_symbols():
             "bsi_field_adjoint_noalloc", "bsi_set_tile_configs", "bsi_get_tile_config", "bsi_probe_fill",
             "bsi_resample_forward", "bsi_resample_backward_workspace_bytes", "bsi_resample_backward",
             "bsi_scalar_forward", "bsi_field_forward_variant", "bsi_geom_rational_init",
-            "bsi_field_forward_rational", "bsi_selftest_lost_copy"]
+            "bsi_field_forward_rational", "bsi_rational_adjoint_workspace_bytes", "bsi_field_adjoint_rational",
+            "bsi_selftest_lost_copy"]
 
 
 def bsi_set_tile_configs(configs) -> None:
@@ -384,6 +387,31 @@ def bsi_field_forward_rational(phi, shape, num, den, off=(0, 0, 0), out=None, st
     st = library().bsi_field_forward_rational(ctypes.byref(g), phi.data_ptr(), out.data_ptr(),
                                               _stream(stream, phi.device))
     _check(st, "bsi_field_forward_rational")
+    return out
+
+
+def bsi_rational_adjoint_workspace_bytes(shape, num, den, off=(0, 0, 0)) -> int:
+    return int(library().bsi_rational_adjoint_workspace_bytes(ctypes.byref(make_geom_rational(shape, num, den, off))))
+
+
+def bsi_field_adjoint_rational(grad_field, num, den, off=(0, 0, 0), out=None, workspace=None, stream=None):
+    """Transpose of bsi_field_forward_rational: dphi [nz, ny, nx, 3] from
+    grad_field [Z, Y, X, 3] (FP32); num, den, off in (z, y, x) order."""
+    _need(grad_field, "grad_field", torch.float32)
+    if grad_field.dim() != 4 or grad_field.shape[3] != 3:
+        raise ValueError("grad_field must be [Z, Y, X, 3]")
+    shape = tuple(int(s) for s in grad_field.shape[:3])
+    grid = rational_grid_shape(shape, num, den, off)
+    if out is None:
+        out = torch.empty(grid + (3,), dtype=torch.float32, device=grad_field.device)
+    _need(out, "out", torch.float32, grid + (3,))
+    g = make_geom_rational(shape, num, den, off)
+    nbytes = int(library().bsi_rational_adjoint_workspace_bytes(ctypes.byref(g)))
+    ws, wsb = _workspace(nbytes, grad_field.device, workspace)
+    st = library().bsi_field_adjoint_rational(ctypes.byref(g), grad_field.data_ptr(), out.data_ptr(),
+                                              ws.data_ptr() if ws is not None else None, wsb,
+                                              _stream(stream, grad_field.device))
+    _check(st, "bsi_field_adjoint_rational")
     return out
 
 

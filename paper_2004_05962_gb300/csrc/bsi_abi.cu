@@ -954,6 +954,23 @@ static bsi_status check_rational(const bsi_geom_rational* g) {
     return BSI_OK;
 }
 
+static RatDesc rat_desc(const bsi_geom_rational& g) {
+    RatDesc d;
+    std::memset(&d, 0, sizeof d);
+    d.X = (int)g.X;
+    d.Y = (int)g.Y;
+    d.Z = (int)g.Z;
+    for (int a = 0; a < 3; ++a) {
+        d.num[a] = g.num[a];
+        d.den[a] = g.den[a];
+        d.off[a] = g.off[a];
+    }
+    d.nx = (int)g.nx;
+    d.ny = (int)g.ny;
+    d.nz = (int)g.nz;
+    return d;
+}
+
 bsi_status bsi_field_forward_rational(const bsi_geom_rational* g, const float* phi, float* field,
                                       bsi_stream_t stream) {
     bsi_status st = check_rational(g);
@@ -961,23 +978,39 @@ bsi_status bsi_field_forward_rational(const bsi_geom_rational* g, const float* p
     if (g->X == 0 || g->Y == 0 || g->Z == 0) return BSI_OK;
     if (!phi || !field) return BSI_ERR_NULL;
     if (misaligned(phi, 4) || misaligned(field, 4)) return BSI_ERR_ALIGN;
-    RatDesc d;
-    std::memset(&d, 0, sizeof d);
-    d.X = (int)g->X;
-    d.Y = (int)g->Y;
-    d.Z = (int)g->Z;
-    for (int a = 0; a < 3; ++a) {
-        d.num[a] = g->num[a];
-        d.den[a] = g->den[a];
-        d.off[a] = g->off[a];
-    }
-    d.nx = (int)g->nx;
-    d.ny = (int)g->ny;
-    d.nz = (int)g->nz;
+    RatDesc d = rat_desc(*g);
     d.phi = phi;
     d.field = field;
     (void)cudaGetLastError();
     const cudaError_t e = launch_forward_rational(d, reinterpret_cast<cudaStream_t>(stream), nullptr);
+    return e == cudaSuccess ? BSI_OK : cuda_fail(e);
+}
+
+size_t bsi_rational_adjoint_workspace_bytes(const bsi_geom_rational* g) {
+    if (check_rational(g) != BSI_OK || g->X == 0 || g->Y == 0 || g->Z == 0) return 0;
+    return (size_t)rational_adjoint_plan(rat_desc(*g)).part_floats * sizeof(float);
+}
+
+bsi_status bsi_field_adjoint_rational(const bsi_geom_rational* g, const float* grad_field, float* grad_phi,
+                                      void* workspace, size_t workspace_bytes, bsi_stream_t stream) {
+    bsi_status st = check_rational(g);
+    if (st != BSI_OK) return st;
+    if (!grad_phi) return BSI_ERR_NULL;
+    if (misaligned(grad_phi, 4)) return BSI_ERR_ALIGN;
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (g->X == 0 || g->Y == 0 || g->Z == 0) {   // no voxel: the gradient is zero
+        (void)cudaGetLastError();
+        const cudaError_t e = cudaMemsetAsync(grad_phi, 0, (size_t)(g->nx * g->ny * g->nz) * 3 * sizeof(float), s);
+        return e == cudaSuccess ? BSI_OK : cuda_fail(e);
+    }
+    if (!grad_field) return BSI_ERR_NULL;
+    if (misaligned(grad_field, 4)) return BSI_ERR_ALIGN;
+    const RatDesc d = rat_desc(*g);
+    const size_t need = (size_t)rational_adjoint_plan(d).part_floats * sizeof(float);
+    if (!workspace || workspace_bytes < need) return BSI_ERR_WORKSPACE;
+    if (misaligned(workspace, 16)) return BSI_ERR_ALIGN;
+    (void)cudaGetLastError();
+    const cudaError_t e = launch_adjoint_rational(d, grad_field, grad_phi, static_cast<float*>(workspace), s);
     return e == cudaSuccess ? BSI_OK : cuda_fail(e);
 }
 

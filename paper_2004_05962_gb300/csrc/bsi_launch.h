@@ -48,6 +48,14 @@ cudaError_t variants_err_read_clear(unsigned* out, cudaStream_t s);
 // Non-integer, non-aligned spacing (bsi_rational.cu).
 int rational_warps_per_cta(int nx);
 cudaError_t launch_forward_rational(const RatDesc& d, cudaStream_t s, LaunchInfo* info);
+// Adjoint of the non-integer-spacing path: its unit counts and partial-sum
+// floats (the workspace), and its two launches (partials, reduce).
+struct RatAdjPlan {
+    int ncx, ncy, ncz, nsx, sc, zsplit;
+    long long part_floats;
+};
+RatAdjPlan rational_adjoint_plan(const RatDesc& d);
+cudaError_t launch_adjoint_rational(const RatDesc& d, const float* grad, float* dphi, float* part, cudaStream_t s);
 cudaError_t rational_err_read_clear(unsigned* out, cudaStream_t s);
 
 // Scalar (one-channel) interpolation: Eq. 1 with grid [nz][ny][nx], output [Z][Y][X].

@@ -121,6 +121,7 @@ constexpr int kRatStripMinCell = 4;                            // x-spacing num/
 constexpr int kRatStripVox = kGroupCells * kRatStripMaxCell;   // voxels of one staged row segment
 constexpr int kRatStripBuf = 12 * kRatStripVox + 16;           // + the segment's 16-byte phase
 constexpr int kRatStripWarps = 8;
+constexpr int kRatTableMaxX = 2048;   // x cells and weights tabulated per CTA up to this width
 constexpr int kRatCellMax = 64;   // rows (planes) of a y-cell (z-cell): spacing <= 64
 constexpr int kRatWeightBytes = 2 * kRatCellMax * 16;   // per warp: the unit's y and z weights
 
@@ -279,11 +280,326 @@ __global__ void __launch_bounds__(kRatStripWarps * 32, 2)
     __syncwarp();
 }
 
+// --------------------------------------------------------------- adjoint
+//
+// The transpose of Eq. 1 on such a grid (the gradient with respect to the
+// control points).  bsi_rational_adjoint_kernel walks the strip kernel's units
+// (z-cell part x y-cell x strip of sc x-cells): the unit's gradient rows arrive
+// by bulk copy in a ring of kRatAdjStages buffers per warp; lane l < sc gathers
+// the voxels of its cell with their four x weights, the column of lane l
+// collects the taps of the cells 0..3 lanes below it by shuffles, and y and z
+// are accumulated in registers.  Each unit writes the partial sums of its 4
+// planes x 4 rows x 32 columns; bsi_rational_adjoint_reduce_kernel then sums,
+// per control point, the partials of every unit that covers it in a fixed
+// order: deterministic, no atomics.
+
+constexpr int kRatAdjStages = 3;
+constexpr int kRatAdjBuf = 12 * kRatStripVox + 32;                 // a row segment + its 16-byte phase
+constexpr int kRatAdjWarpBytes = kRatAdjStages * (16 + kRatAdjBuf);  // mbarriers + ring, per warp
+constexpr int kRatAdjWarps = 8;
+constexpr int kRatAdjMinUnits = 2048;   // z-cells are split while there are fewer units (device-independent)
+constexpr int kRatPartFloats = 4 * 4 * 32 * 3;   // per unit: planes x rows x columns x channels
+
+template <bool TABLE, int CMAX>
+__global__ void __launch_bounds__(kRatAdjWarps * 32, 2)
+    bsi_rational_adjoint_kernel(const __grid_constant__ RatDesc d, const float* __restrict__ grad,
+                                float* __restrict__ part, int ncx, int ncy, int ncz, int nsx, int sc, int zsplit) {
+    extern __shared__ __align__(16) unsigned char radj[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpc = blockDim.x >> 5;
+    unsigned char* wsm = radj + (size_t)warp * kRatAdjWarpBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm);          // bars[s] in 16-byte slots' first 8 bytes
+    unsigned char* bufs = wsm + 16 * kRatAdjStages;
+    float4* xw = reinterpret_cast<float4*>(radj + (size_t)wpc * kRatAdjWarpBytes);
+    float4* yw = xw + (TABLE ? d.X : 0) + (size_t)warp * 2 * kRatCellMax;
+    float4* zw = yw + kRatCellMax;
+    if (lane == 0) {
+        for (int st = 0; st < kRatAdjStages; ++st) mbar_init(bars + 2 * st, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (TABLE)
+        for (int x = threadIdx.x; x < d.X; x += blockDim.x) {
+            float B[4];
+            const int f = (x * d.den[0] + d.off[0]) / d.num[0];
+            axis_weights(x, f, d.num[0], d.den[0], d.off[0], B);
+            xw[x] = make_float4(B[0], B[1], B[2], B[3]);
+        }
+    __syncthreads();
+    const uintptr_t gbase = reinterpret_cast<uintptr_t>(grad);
+    const uintptr_t A0 = ceil16(gbase);
+    const uintptr_t A1 = floor16(gbase + (uintptr_t)(12LL * d.X * d.Y * d.Z));
+    unsigned q = 0;   // row copies this warp has consumed (ring stage and phase)
+    bool ok = true;
+    const long long units = (long long)ncz * zsplit * ncy * nsx;
+    for (long long un = (long long)blockIdx.x * wpc + warp; ok && un < units; un += (long long)gridDim.x * wpc) {
+        const int xs = (int)(un % nsx);
+        const long long t = un / nsx;
+        const int jy = (int)(t % ncy);
+        const long long t2 = t / ncy;
+        const int zp = (int)(t2 % zsplit), kz = (int)(t2 / zsplit);
+        const int zc0 = cell_first(kz, d.num[2], d.den[2], d.off[2]);
+        const int zcn = imin(d.Z, cell_first(kz + 1, d.num[2], d.den[2], d.off[2])) - zc0;
+        const int z0 = zc0 + zcn * zp / zsplit, z1 = zc0 + zcn * (zp + 1) / zsplit;
+        const int y0 = cell_first(jy, d.num[1], d.den[1], d.off[1]);
+        const int y1 = imin(d.Y, cell_first(jy + 1, d.num[1], d.den[1], d.off[1]));
+        const int c0 = xs * sc, col = c0 + lane;
+        const bool owns = lane < sc && col < ncx;
+        const int xa = owns ? cell_first(col, d.num[0], d.den[0], d.off[0]) : 0;
+        const int xb = owns ? imin(d.X, cell_first(col + 1, d.num[0], d.den[0], d.off[0])) : 0;
+        const int sx0 = cell_first(c0, d.num[0], d.den[0], d.off[0]);
+        const int sx1 = imin(d.X, cell_first(imin(c0 + sc, ncx), d.num[0], d.den[0], d.off[0]));
+        const int nbytes = 12 * (sx1 - sx0);
+        const int nyu = y1 - y0, rows = (z1 - z0) * nyu;
+        __syncwarp();   // the previous unit's weights are read
+        for (int i = lane; i < nyu; i += 32) {
+            float B[4];
+            axis_weights(y0 + i, jy, d.num[1], d.den[1], d.off[1], B);
+            yw[i] = make_float4(B[0], B[1], B[2], B[3]);
+        }
+        for (int i = lane; i < z1 - z0; i += 32) {
+            float B[4];
+            axis_weights(z0 + i, kz, d.num[2], d.den[2], d.off[2], B);
+            zw[i] = make_float4(B[0], B[1], B[2], B[3]);
+        }
+        __syncwarp();
+
+        // row k of the unit: plane z0 + k / nyu, row y0 + k % nyu, voxels [sx0, sx1)
+        const unsigned q0 = q;
+        auto row_addr = [&](int k) -> uintptr_t {
+            const long long z = z0 + k / nyu, y = y0 + k % nyu;
+            return gbase + (uintptr_t)(12LL * ((z * d.Y + y) * d.X + sx0));
+        };
+        auto issue = [&](int k) {   // lane 0: row k into ring stage (q0 + k) % kRatAdjStages
+            const unsigned st = (q0 + (unsigned)k) % kRatAdjStages;
+            const RowLoad L = row_load(reinterpret_cast<const unsigned char*>(row_addr(k)), nbytes, A0, A1);
+            if (L.s1 > L.s0) {
+                mbar_arrive_expect_tx(bars + 2 * st, (uint32_t)(L.s1 - L.s0));
+                bulk_load(bufs + st * kRatAdjBuf + (L.s0 - L.lo), reinterpret_cast<const void*>(L.s0),
+                          (uint32_t)(L.s1 - L.s0), bars + 2 * st);
+            } else {
+                mbar_arrive(bars + 2 * st);
+            }
+        };
+        if (lane == 0)
+            for (int k = 0; k < rows && k < kRatAdjStages; ++k) issue(k);
+
+        float hz[4][4][3];
+#pragma unroll
+        for (int n = 0; n < 4; ++n)
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) hz[n][m][c] = 0.f;
+        int k = 0;
+        for (int z = z0; ok && z < z1; ++z) {
+            float hy[4][3];
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) hy[m][c] = 0.f;
+            for (int y = y0; y < y1; ++y, ++k) {
+                const unsigned qq = q0 + (unsigned)k, st = qq % kRatAdjStages;
+                if (!mbar_wait_bounded(bars + 2 * st, (qq / kRatAdjStages) & 1u)) {
+                    // a bulk copy never completed: record it, give the copies still in
+                    // flight a bounded chance to land, and stop this warp
+                    if (lane == 0) atomicOr(&g_err, kErrTimeout);
+                    for (int p = k + 1; p < rows && p < k + kRatAdjStages; ++p) {
+                        const unsigned qp = q0 + (unsigned)p;
+                        (void)mbar_wait_bounded(bars + 2 * (qp % kRatAdjStages), (qp / kRatAdjStages) & 1u);
+                    }
+                    ok = false;
+                    break;
+                }
+                const uintptr_t g = row_addr(k);
+                unsigned char* sb = bufs + st * kRatAdjBuf + (g & 15);
+                if (g < A0 || g + (uintptr_t)nbytes > A1) {
+                    // first or last row of the array: its elements outside the bulk copy
+                    const RowLoad L = row_load(reinterpret_cast<const unsigned char*>(g), nbytes, A0, A1);
+                    for (int i = lane; i < nbytes / 4; i += 32) {
+                        const uintptr_t a = g + 4u * (uintptr_t)i;
+                        if (a < L.s0 || a >= L.s1) reinterpret_cast<float*>(sb)[i] = *reinterpret_cast<const float*>(a);
+                    }
+                }
+                __syncwarp();
+                float q4[4][3];
+#pragma unroll
+                for (int l = 0; l < 4; ++l)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) q4[l][c] = 0.f;
+                // x-transpose of the lane's cell: q_l += B_l(x) G(x), voxels in order
+                auto gather = [&](int x) {
+                    float B[4];
+                    if (TABLE) {
+                        const float4 w = xw[x];
+                        B[0] = w.x;
+                        B[1] = w.y;
+                        B[2] = w.z;
+                        B[3] = w.w;
+                    } else {
+                        axis_weights(x, col, d.num[0], d.den[0], d.off[0], B);
+                    }
+                    BSI_GUARD(x >= sx0 && (int)(g & 15) + 12 * (x - sx0) + 12 <= kRatAdjBuf, kErrStage, &g_err) {
+                        const uint32_t sv = smem_u32(sb) + 12u * (uint32_t)(x - sx0);
+                        const float g0 = lds_f32(sv), g1 = lds_f32(sv + 4), g2 = lds_f32(sv + 8);
+#pragma unroll
+                        for (int l = 0; l < 4; ++l) {
+                            q4[l][0] = fmaf(B[l], g0, q4[l][0]);
+                            q4[l][1] = fmaf(B[l], g1, q4[l][1]);
+                            q4[l][2] = fmaf(B[l], g2, q4[l][2]);
+                        }
+                    }
+                };
+                if (CMAX > 0) {   // CMAX >= ceil(num / den) >= xb - xa: unrolled
+#pragma unroll
+                    for (int i = 0; i < (CMAX > 0 ? CMAX : 1); ++i) {
+                        if (xa + i >= xb) break;
+                        gather(xa + i);
+                    }
+                } else {
+                    for (int x = xa; x < xb; ++x) gather(x);
+                }
+                // this ring buffer may be refilled once every lane has read it
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0 && k + kRatAdjStages < rows) issue(k + kRatAdjStages);
+                // column sums: column c0 + lane collects tap l of the cell l lanes below
+                const float4 wy = yw[y - y0];
+                const float By[4] = {wy.x, wy.y, wy.z, wy.w};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float t1 = __shfl_up_sync(kFull, q4[1][c], 1);
+                    const float t2 = __shfl_up_sync(kFull, q4[2][c], 2);
+                    const float t3 = __shfl_up_sync(kFull, q4[3][c], 3);
+                    const float h = q4[0][c] + (lane >= 1 ? t1 : 0.f) + (lane >= 2 ? t2 : 0.f) + (lane >= 3 ? t3 : 0.f);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) hy[m][c] = fmaf(By[m], h, hy[m][c]);
+                }
+            }
+            if (!ok) break;
+            const float4 wz = zw[z - z0];
+            const float Bz[4] = {wz.x, wz.y, wz.z, wz.w};
+#pragma unroll
+            for (int n = 0; n < 4; ++n)
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) hz[n][m][c] = fmaf(Bz[n], hy[m][c], hz[n][m][c]);
+        }
+        q = q0 + (unsigned)rows;
+        if (!ok) break;
+        // the unit's partial sums: [plane n][row m][column lane][channel]
+        float* P = part + un * kRatPartFloats;
+#pragma unroll
+        for (int n = 0; n < 4; ++n)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                float* e = P + ((n * 4 + m) * 32 + lane) * 3;
+                e[0] = hz[n][m][0];
+                e[1] = hz[n][m][1];
+                e[2] = hz[n][m][2];
+            }
+    }
+    __syncwarp();
+    if (lane == 0)
+        for (int st = 0; st < kRatAdjStages; ++st) mbar_inval(bars + 2 * st);
+}
+
+// One thread per stored control point (gx, gy, gz): the units that cover it are
+// z-cells kz = gz - n (n = 0..3), every part of each, y-cells jy = gy - m, and
+// the strips xs whose 32 columns [xs sc, xs sc + 32) hold gx.
+__global__ void __launch_bounds__(256, 4)
+    bsi_rational_adjoint_reduce_kernel(const __grid_constant__ RatDesc d, const float* __restrict__ part,
+                                       float* __restrict__ dphi, int ncx, int ncy, int ncz, int nsx, int sc,
+                                       int zsplit) {
+    (void)ncx;
+    const long long npts = (long long)d.nx * d.ny * d.nz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npts; p += stride) {
+        const int gx = (int)(p % d.nx);
+        const long long t = p / d.nx;
+        const int gy = (int)(t % d.ny), gz = (int)(t / d.ny);
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        for (int kz = imax(0, gz - 3); kz <= imin(gz, ncz - 1); ++kz)
+            for (int zp = 0; zp < zsplit; ++zp)
+                for (int jy = imax(0, gy - 3); jy <= imin(gy, ncy - 1); ++jy)
+                    for (int xs = imin(nsx - 1, gx / sc); xs >= 0 && gx - xs * sc < 32; --xs) {
+                        const long long un = (((long long)kz * zsplit + zp) * ncy + jy) * nsx + xs;
+                        const float* e = part + un * kRatPartFloats + (((gz - kz) * 4 + (gy - jy)) * 32 + (gx - xs * sc)) * 3;
+                        s0 += e[0];
+                        s1 += e[1];
+                        s2 += e[2];
+                    }
+        dphi[3 * p] = s0;
+        dphi[3 * p + 1] = s1;
+        dphi[3 * p + 2] = s2;
+    }
+}
+
+// Cells per axis, strips and z-parts of the adjoint's units (host, shared with
+// the workspace query).
+RatAdjPlan rational_adjoint_plan(const RatDesc& d) {
+    RatAdjPlan pl;
+    pl.ncx = (int)(((long long)(d.X - 1) * d.den[0] + d.off[0]) / d.num[0]) + 1;
+    pl.ncy = (int)(((long long)(d.Y - 1) * d.den[1] + d.off[1]) / d.num[1]) + 1;
+    pl.ncz = (int)(((long long)(d.Z - 1) * d.den[2] + d.off[2]) / d.num[2]) + 1;
+    const int cmax = (d.num[0] + d.den[0] - 1) / d.den[0];
+    pl.sc = imin(kGroupCells, kRatStripVox / cmax);
+    pl.nsx = (int)cdiv(pl.ncx, pl.sc);
+    pl.zsplit = 1;
+    while (2 * pl.zsplit <= d.num[2] / d.den[2] &&
+           (long long)pl.ncz * pl.zsplit * pl.ncy * pl.nsx < kRatAdjMinUnits)
+        pl.zsplit *= 2;
+    pl.part_floats = (long long)pl.ncz * pl.zsplit * pl.ncy * pl.nsx * kRatPartFloats;
+    return pl;
+}
+
+cudaError_t launch_adjoint_rational(const RatDesc& d, const float* grad, float* dphi, float* part,
+                                    cudaStream_t s) {
+    const RatAdjPlan pl = rational_adjoint_plan(d);
+    const int cmax = (d.num[0] + d.den[0] - 1) / d.den[0];
+    const bool table = d.X <= kRatTableMaxX;
+    const int table_bytes = table ? 16 * d.X : 0;
+    const int per_warp = kRatAdjWarpBytes + 2 * kRatCellMax * 16;
+    int wpc = (kSmemBudget - table_bytes) / per_warp;
+    wpc = wpc < 1 ? 1 : (wpc > kRatAdjWarps ? kRatAdjWarps : wpc);
+    const int threads = wpc * 32, smem = wpc * per_warp + table_bytes;
+    const void* kern = nullptr;
+#define BSI_RAT_ADJ_KERN(CM)                                                                      \
+    kern = table ? reinterpret_cast<const void*>(bsi_rational_adjoint_kernel<true, CM>)           \
+                 : reinterpret_cast<const void*>(bsi_rational_adjoint_kernel<false, CM>)
+    if (cmax <= 4) BSI_RAT_ADJ_KERN(4);
+    else if (cmax <= 8) BSI_RAT_ADJ_KERN(8);
+    else BSI_RAT_ADJ_KERN(0);
+#undef BSI_RAT_ADJ_KERN
+    KernelFacts f;
+    cudaError_t e = kernel_facts(kern, threads, smem, &f);
+    if (e != cudaSuccess) return e;
+    const long long units = pl.part_floats / kRatPartFloats;
+    const long long want = cdiv(units, wpc);
+    const long long cap = (long long)f.sms * f.ctas_per_sm;
+    const int grid = (int)(want < cap ? want : cap);
+    if (grid > 0) {
+        int ncx = pl.ncx, ncy = pl.ncy, ncz = pl.ncz, nsx = pl.nsx, sc = pl.sc, zsplit = pl.zsplit;
+        const float* gptr = grad;
+        void* args[] = {const_cast<RatDesc*>(&d), (void*)&gptr, (void*)&part, (void*)&ncx, (void*)&ncy,
+                        (void*)&ncz, (void*)&nsx, (void*)&sc, (void*)&zsplit};
+        e = cudaLaunchKernel(kern, dim3(grid), dim3(threads), args, (size_t)smem, s);
+        if (e != cudaSuccess) return e;
+    }
+    const long long npts = (long long)d.nx * d.ny * d.nz;
+    const long long rgrid = cdiv(npts, 256);
+    const int rg = (int)(rgrid < 4LL * f.sms * 8 ? rgrid : 4LL * f.sms * 8);
+    if (rg > 0)
+        bsi_rational_adjoint_reduce_kernel<<<rg, 256, 0, s>>>(d, part, dphi, pl.ncx, pl.ncy, pl.ncz, pl.nsx, pl.sc,
+                                                              pl.zsplit);
+    return cudaGetLastError();
+}
+
 // Rows per warp of the windowed kernel, and the grid widths it takes (its
 // shared memory per warp: 4 z-contracted grid rows + the line, 60 nx bytes).
 constexpr int kRatRun = 16;
 constexpr int kRatWindowMaxNx = 1024;
-constexpr int kRatTableMaxX = 2048;   // x cells and weights tabulated per CTA up to this width
 
 // A warp takes a run of `run` (<= kRatRun) consecutive rows of one voxel plane z.  It keeps
 // the z-contraction of the four grid rows the current row needs,

@@ -270,3 +270,37 @@ def test_rational_geometry_and_validation_before_cuda(lib):
                 ((5, 5, 5), (2000, 2, 2), (0, 0, 0))]:      # denominator beyond the limit
         with pytest.raises(B.BsiError):
             B.make_geom_rational((7, 9, 11), *bad)
+
+
+def test_rational_adjoint_workspace_and_validation_before_cuda(lib):
+    """The adjoint's workspace is 6 KB per unit (z-cell part x y-cell x strip of
+    up to 29 x-cells; z-cells split while there are fewer than 2048 units), and
+    the argument checks come before any CUDA call."""
+    fake = 0x7F0000000000  # never dereferenced: validation fails first
+    cases = [((300, 512, 512), (47, 47, 47), (10, 10, 10), (3, 0, 9)),
+             ((7, 9, 11), (5, 7, 9), (2, 2, 2), (0, 3, 1)),
+             ((10, 10, 33), (640, 13, 23), (10, 5, 7), (639, 4, 22))]
+    for shape, num, den, off in cases:
+        g = B.make_geom_rational(shape, num, den, off)
+        ncell = [((N - 1) * d + o) // n + 1 for N, n, d, o in zip(shape, num, den, off)]   # (z, y, x)
+        cmax = -(-num[2] // den[2])
+        sc = min(29, 232 // cmax)
+        nsx = -(-ncell[2] // sc)
+        zsplit = 1
+        while 2 * zsplit <= num[0] // den[0] and ncell[0] * zsplit * ncell[1] * nsx < 2048:
+            zsplit *= 2
+        want = ncell[0] * zsplit * ncell[1] * nsx * 4 * 4 * 32 * 3 * 4
+        assert lib.bsi_rational_adjoint_workspace_bytes(ctypes.byref(g)) == want, (shape, num)
+    g = B.make_geom_rational((7, 9, 11), (5, 7, 9), (2, 2, 2), (0, 3, 1))
+    need = lib.bsi_rational_adjoint_workspace_bytes(ctypes.byref(g))
+    ar = lib.bsi_field_adjoint_rational
+    assert ar(ctypes.byref(g), fake, None, fake, need, None) == 1          # grad_phi NULL
+    assert ar(ctypes.byref(g), fake, fake + 2, fake, need, None) == 6      # grad_phi misaligned
+    assert ar(ctypes.byref(g), None, fake, fake, need, None) == 1          # grad_field NULL
+    assert ar(ctypes.byref(g), fake + 2, fake, fake, need, None) == 6      # grad_field misaligned
+    assert ar(ctypes.byref(g), fake, fake, None, need, None) == 7          # no workspace
+    assert ar(ctypes.byref(g), fake, fake, fake, need - 4, None) == 7      # short workspace
+    assert ar(ctypes.byref(g), fake, fake, fake + 4, need, None) == 6      # workspace misaligned
+    g.nx += 1
+    assert ar(ctypes.byref(g), fake, fake, fake, need, None) == 4
+    assert lib.bsi_rational_adjoint_workspace_bytes(ctypes.byref(g)) == 0

@@ -157,6 +157,20 @@ def test_ct_rational_forward_sampled():
     assert float(np.max(np.abs(got - want))) <= FWD_TOL * float(np.max(np.abs(phi)))
 
 
+def test_ct_rational_adjoint_sampled():
+    """The adjoint of the non-integer spacing workload (512x512x300 at 4.7 voxels,
+    shifted lattice) at sampled control points, including the grid's corners."""
+    shape, num, den, off = (300, 512, 512), (47, 47, 47), (10, 10, 10), (3, 0, 9)
+    G = synth.normal_field(shape, seed=10)
+    dphi = P.bsi_field_adjoint_rational(torch.from_numpy(G).to(dev()), num, den, off)
+    torch.cuda.synchronize()
+    gpts = synth.sample_grid_points(P.rational_grid_shape(shape, num, den, off), 300, seed=10)
+    want = oracle.adjoint_rational_points(G, num, den, off, gpts)
+    gi = torch.from_numpy(gpts).to(dev())
+    gd = dphi[gi[:, 2], gi[:, 1], gi[:, 0]].double().cpu().numpy()
+    assert float(np.max(np.abs(gd - want))) <= ADJ_TOL * max(float(np.max(np.abs(want))), 1e-30) * 10
+
+
 def test_ct_scalar_zoom_sampled():
     """The bench's scalar workload: a 4x zoom of a 128 x 128 x 75 image (plus
     border) to 512 x 512 x 300, FP32 and BF16."""

@@ -7,7 +7,7 @@ import torch
 import oracle
 import paper_2004_05962_gb300 as P
 from paper_2004_05962_gb300 import synth
-from gpu_util import FWD_TOL, dev
+from gpu_util import ADJ_TOL, FWD_TOL, dev
 
 pytestmark = pytest.mark.gpu
 
@@ -57,3 +57,58 @@ def test_rational_with_integer_spacing_matches_the_strip_kernel():
     b = P.bsi_field_forward_rational(phi, shape, spacing, (1, 1, 1), (0, 0, 0))
     torch.cuda.synchronize()
     assert float((a - b).abs().max()) <= 2 * FWD_TOL * 2.0
+
+
+@pytest.mark.parametrize("shape,num,den,off", CASES, ids=[f"{c[0]}-{c[1]}/{c[2]}+{c[3]}" for c in CASES])
+def test_rational_adjoint_matches_oracle(shape, num, den, off):
+    """Transpose of the non-integer-spacing forward against the FP64 scatter
+    oracle, element by element over the whole grid."""
+    rng = np.random.default_rng(3 * sum(shape) + sum(den))
+    G = rng.standard_normal(shape + (3,)).astype(np.float32)
+    got = P.bsi_field_adjoint_rational(torch.from_numpy(G).to(dev()), num, den, off)
+    torch.cuda.synchronize()
+    want = oracle.adjoint_rational(G, num, den, off)
+    assert got.shape == want.shape
+    err = float(np.max(np.abs(got.double().cpu().numpy() - want)))
+    assert err <= ADJ_TOL * max(float(np.max(np.abs(want))), 1e-30), err
+    assert P.bsi_check_device_status() == 0
+
+
+def test_rational_adjoint_is_the_transpose_and_deterministic():
+    """<forward(phi), G> = <phi, adjoint(G)> on the GPU (FP32 sums, relative
+    1e-5), and two adjoint calls give the same bits."""
+    shape, num, den, off = (30, 41, 97), (13, 11, 17), (2, 2, 4), (1, 0, 3)
+    rng = np.random.default_rng(71)
+    phi = torch.from_numpy(rng.uniform(-2, 2, P.rational_grid_shape(shape, num, den, off) + (3,))
+                           .astype(np.float32)).to(dev())
+    G = torch.from_numpy(rng.standard_normal(shape + (3,)).astype(np.float32)).to(dev())
+    T = P.bsi_field_forward_rational(phi, shape, num, den, off)
+    a = P.bsi_field_adjoint_rational(G, num, den, off)
+    b = P.bsi_field_adjoint_rational(G, num, den, off)
+    torch.cuda.synchronize()
+    lhs = float((T.double() * G.double()).sum())
+    rhs = float((phi.double() * a.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), 1.0)
+    assert torch.equal(a, b)
+
+
+def test_rational_adjoint_of_an_empty_volume_is_zero():
+    shape, num, den, off = (0, 5, 7), (5, 5, 5), (2, 2, 2), (0, 0, 0)
+    G = torch.empty(shape + (3,), device=dev())
+    out = torch.full(P.rational_grid_shape(shape, num, den, off) + (3,), 7.0, device=dev())
+    P.bsi_field_adjoint_rational(G, num, den, off, out=out)
+    torch.cuda.synchronize()
+    assert float(out.abs().max()) == 0.0
+
+
+def test_field_rational_autograd_uses_the_adjoint():
+    """field_rational's backward is bsi_field_adjoint_rational, bit for bit."""
+    shape, num, den, off = (20, 16, 70), (47, 47, 47), (10, 10, 10), (3, 0, 9)
+    rng = np.random.default_rng(72)
+    phi = torch.from_numpy(rng.uniform(-2, 2, P.rational_grid_shape(shape, num, den, off) + (3,))
+                           .astype(np.float32)).to(dev()).requires_grad_()
+    W = torch.from_numpy(rng.standard_normal(shape + (3,)).astype(np.float32)).to(dev())
+    (P.field_rational(phi, shape, num, den, off) * W).sum().backward()
+    want = P.bsi_field_adjoint_rational(W, num, den, off)
+    torch.cuda.synchronize()
+    assert torch.equal(phi.grad, want)
