@@ -51,7 +51,7 @@ cudaError_t launch_forward_rational(const RatDesc& d, cudaStream_t s, LaunchInfo
 // Adjoint of the non-integer-spacing path: its unit counts and partial-sum
 // floats (the workspace), and its two launches (partials, reduce).
 struct RatAdjPlan {
-    int ncx, ncy, ncz, nsx, sc, zsplit;
+    int ncx, ncy, ncz, nsx, sc, zc;   // cells per axis, strips, cells per strip, z-cells per unit
     long long part_floats;
 };
 RatAdjPlan rational_adjoint_plan(const RatDesc& d);

@@ -283,36 +283,52 @@ __global__ void __launch_bounds__(kRatStripWarps * 32, 2)
 // --------------------------------------------------------------- adjoint
 //
 // The transpose of Eq. 1 on such a grid (the gradient with respect to the
-// control points).  bsi_rational_adjoint_kernel walks the strip kernel's units
-// (z-cell part x y-cell x strip of sc x-cells): the unit's gradient rows arrive
+// control points).  bsi_rational_adjoint_kernel walks units of zc consecutive
+// z-cells x one y-cell x a strip of sc x-cells: the unit's gradient rows arrive
 // by bulk copy in a ring of kRatAdjStages buffers per warp; lane l < sc gathers
 // the voxels of its cell with their four x weights, the column of lane l
-// collects the taps of the cells 0..3 lanes below it by shuffles, and y and z
-// are accumulated in registers.  Each unit writes the partial sums of its 4
-// planes x 4 rows x 32 columns; bsi_rational_adjoint_reduce_kernel then sums,
-// per control point, the partials of every unit that covers it in a fixed
-// order: deterministic, no atomics.
+// collects the taps of the cells 0..3 lanes below it by shuffles, y is summed
+// in registers and z in a rolling window of four grid planes, one of which is
+// complete (and written) after each z-cell.  Each unit writes the partial sums
+// of its zc + 3 planes x 4 rows x 32 columns; bsi_rational_adjoint_reduce_kernel
+// then sums, per control point, the partials of every unit that covers it in
+// a fixed order: deterministic, no atomics.
 
-constexpr int kRatAdjStages = 3;
-constexpr int kRatAdjBuf = 12 * kRatStripVox + 32;                 // a row segment + its 16-byte phase
-constexpr int kRatAdjWarpBytes = kRatAdjStages * (16 + kRatAdjBuf);  // mbarriers + ring, per warp
+constexpr int kRatAdjStages = 4;
 constexpr int kRatAdjWarps = 8;
-constexpr int kRatAdjMinUnits = 2048;   // z-cells are split while there are fewer units (device-independent)
-constexpr int kRatPartFloats = 4 * 4 * 32 * 3;   // per unit: planes x rows x columns x channels
+// Ring buffer bytes for row segments of up to nvox voxels (+ the 16-byte phase
+// and the copy's rounding), and a warp's mbarriers + ring.
+BSI_HD int rat_adj_buf(int nvox) { return (12 * nvox + 32 + 15) & ~15; }
+BSI_HD int rat_adj_warp_bytes(int buf) { return kRatAdjStages * (16 + buf); }
+constexpr int kRatAdjMaxZc = 4;          // z-cells per unit, at most
+constexpr int kRatAdjMinUnits = 6000;    // fewer z-cells per unit while there are fewer units (device-independent)
+constexpr int kRatPartPlane = 4 * 32 * 3;   // partial floats of one grid plane: rows x columns x channels
+
+// One grid plane of a unit's partial sums: [row m][column lane][channel].
+__device__ __forceinline__ void rat_flush_plane(float* P, const float (&h)[4][3], int lane) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        float* e = P + (m * 32 + lane) * 3;
+        e[0] = h[m][0];
+        e[1] = h[m][1];
+        e[2] = h[m][2];
+    }
+}
 
 template <bool TABLE, int CMAX>
 __global__ void __launch_bounds__(kRatAdjWarps * 32, 2)
     bsi_rational_adjoint_kernel(const __grid_constant__ RatDesc d, const float* __restrict__ grad,
-                                float* __restrict__ part, int ncx, int ncy, int ncz, int nsx, int sc, int zsplit) {
+                                float* __restrict__ part, int ncx, int ncy, int ncz, int nsx, int sc, int zc,
+                                int buf) {
     extern __shared__ __align__(16) unsigned char radj[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int wpc = blockDim.x >> 5;
-    unsigned char* wsm = radj + (size_t)warp * kRatAdjWarpBytes;
+    unsigned char* wsm = radj + (size_t)warp * rat_adj_warp_bytes(buf);
     uint64_t* bars = reinterpret_cast<uint64_t*>(wsm);          // bars[s] in 16-byte slots' first 8 bytes
     unsigned char* bufs = wsm + 16 * kRatAdjStages;
-    float4* xw = reinterpret_cast<float4*>(radj + (size_t)wpc * kRatAdjWarpBytes);
-    float4* yw = xw + (TABLE ? d.X : 0) + (size_t)warp * 2 * kRatCellMax;
+    float4* xw = reinterpret_cast<float4*>(radj + (size_t)wpc * rat_adj_warp_bytes(buf));
+    float4* yw = xw + (TABLE ? d.X : 0) + (size_t)warp * 2 * kRatCellMax;   // the unit's rows, then its planes
     float4* zw = yw + kRatCellMax;
     if (lane == 0) {
         for (int st = 0; st < kRatAdjStages; ++st) mbar_init(bars + 2 * st, 1);
@@ -331,16 +347,15 @@ __global__ void __launch_bounds__(kRatAdjWarps * 32, 2)
     const uintptr_t A1 = floor16(gbase + (uintptr_t)(12LL * d.X * d.Y * d.Z));
     unsigned q = 0;   // row copies this warp has consumed (ring stage and phase)
     bool ok = true;
-    const long long units = (long long)ncz * zsplit * ncy * nsx;
+    const long long nch = cdiv(ncz, zc);
+    const long long units = nch * ncy * nsx;
     for (long long un = (long long)blockIdx.x * wpc + warp; ok && un < units; un += (long long)gridDim.x * wpc) {
         const int xs = (int)(un % nsx);
         const long long t = un / nsx;
         const int jy = (int)(t % ncy);
-        const long long t2 = t / ncy;
-        const int zp = (int)(t2 % zsplit), kz = (int)(t2 / zsplit);
-        const int zc0 = cell_first(kz, d.num[2], d.den[2], d.off[2]);
-        const int zcn = imin(d.Z, cell_first(kz + 1, d.num[2], d.den[2], d.off[2])) - zc0;
-        const int z0 = zc0 + zcn * zp / zsplit, z1 = zc0 + zcn * (zp + 1) / zsplit;
+        const int kz0 = (int)(t / ncy) * zc, kz1 = imin(kz0 + zc, ncz);
+        const int z0 = cell_first(kz0, d.num[2], d.den[2], d.off[2]);
+        const int z1 = imin(d.Z, cell_first(kz1, d.num[2], d.den[2], d.off[2]));
         const int y0 = cell_first(jy, d.num[1], d.den[1], d.off[1]);
         const int y1 = imin(d.Y, cell_first(jy + 1, d.num[1], d.den[1], d.off[1]));
         const int c0 = xs * sc, col = c0 + lane;
@@ -357,9 +372,11 @@ __global__ void __launch_bounds__(kRatAdjWarps * 32, 2)
             axis_weights(y0 + i, jy, d.num[1], d.den[1], d.off[1], B);
             yw[i] = make_float4(B[0], B[1], B[2], B[3]);
         }
+        // the planes' weights (z1 - z0 <= zc ceil(num / den) <= kRatCellMax: the plan's bound)
         for (int i = lane; i < z1 - z0; i += 32) {
             float B[4];
-            axis_weights(z0 + i, kz, d.num[2], d.den[2], d.off[2], B);
+            const int z = z0 + i;
+            axis_weights(z, (z * d.den[2] + d.off[2]) / d.num[2], d.num[2], d.den[2], d.off[2], B);
             zw[i] = make_float4(B[0], B[1], B[2], B[3]);
         }
         __syncwarp();
@@ -375,7 +392,7 @@ __global__ void __launch_bounds__(kRatAdjWarps * 32, 2)
             const RowLoad L = row_load(reinterpret_cast<const unsigned char*>(row_addr(k)), nbytes, A0, A1);
             if (L.s1 > L.s0) {
                 mbar_arrive_expect_tx(bars + 2 * st, (uint32_t)(L.s1 - L.s0));
-                bulk_load(bufs + st * kRatAdjBuf + (L.s0 - L.lo), reinterpret_cast<const void*>(L.s0),
+                bulk_load(bufs + st * buf + (L.s0 - L.lo), reinterpret_cast<const void*>(L.s0),
                           (uint32_t)(L.s1 - L.s0), bars + 2 * st);
             } else {
                 mbar_arrive(bars + 2 * st);
@@ -391,114 +408,124 @@ __global__ void __launch_bounds__(kRatAdjWarps * 32, 2)
             for (int m = 0; m < 4; ++m)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) hz[n][m][c] = 0.f;
+        float* P = part + un * (long long)(zc + 3) * kRatPartPlane;   // the unit's planes kz0 .. kz0 + zc + 2
         int k = 0;
-        for (int z = z0; ok && z < z1; ++z) {
-            float hy[4][3];
-#pragma unroll
-            for (int m = 0; m < 4; ++m)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) hy[m][c] = 0.f;
-            for (int y = y0; y < y1; ++y, ++k) {
-                const unsigned qq = q0 + (unsigned)k, st = qq % kRatAdjStages;
-                if (!mbar_wait_bounded(bars + 2 * st, (qq / kRatAdjStages) & 1u)) {
-                    // a bulk copy never completed: record it, give the copies still in
-                    // flight a bounded chance to land, and stop this warp
-                    if (lane == 0) atomicOr(&g_err, kErrTimeout);
-                    for (int p = k + 1; p < rows && p < k + kRatAdjStages; ++p) {
-                        const unsigned qp = q0 + (unsigned)p;
-                        (void)mbar_wait_bounded(bars + 2 * (qp % kRatAdjStages), (qp / kRatAdjStages) & 1u);
-                    }
-                    ok = false;
-                    break;
-                }
-                const uintptr_t g = row_addr(k);
-                unsigned char* sb = bufs + st * kRatAdjBuf + (g & 15);
-                if (g < A0 || g + (uintptr_t)nbytes > A1) {
-                    // first or last row of the array: its elements outside the bulk copy
-                    const RowLoad L = row_load(reinterpret_cast<const unsigned char*>(g), nbytes, A0, A1);
-                    for (int i = lane; i < nbytes / 4; i += 32) {
-                        const uintptr_t a = g + 4u * (uintptr_t)i;
-                        if (a < L.s0 || a >= L.s1) reinterpret_cast<float*>(sb)[i] = *reinterpret_cast<const float*>(a);
-                    }
-                }
-                __syncwarp();
-                float q4[4][3];
-#pragma unroll
-                for (int l = 0; l < 4; ++l)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) q4[l][c] = 0.f;
-                // x-transpose of the lane's cell: q_l += B_l(x) G(x), voxels in order
-                auto gather = [&](int x) {
-                    float B[4];
-                    if (TABLE) {
-                        const float4 w = xw[x];
-                        B[0] = w.x;
-                        B[1] = w.y;
-                        B[2] = w.z;
-                        B[3] = w.w;
-                    } else {
-                        axis_weights(x, col, d.num[0], d.den[0], d.off[0], B);
-                    }
-                    BSI_GUARD(x >= sx0 && (int)(g & 15) + 12 * (x - sx0) + 12 <= kRatAdjBuf, kErrStage, &g_err) {
-                        const uint32_t sv = smem_u32(sb) + 12u * (uint32_t)(x - sx0);
-                        const float g0 = lds_f32(sv), g1 = lds_f32(sv + 4), g2 = lds_f32(sv + 8);
-#pragma unroll
-                        for (int l = 0; l < 4; ++l) {
-                            q4[l][0] = fmaf(B[l], g0, q4[l][0]);
-                            q4[l][1] = fmaf(B[l], g1, q4[l][1]);
-                            q4[l][2] = fmaf(B[l], g2, q4[l][2]);
-                        }
-                    }
-                };
-                if (CMAX > 0) {   // CMAX >= ceil(num / den) >= xb - xa: unrolled
-#pragma unroll
-                    for (int i = 0; i < (CMAX > 0 ? CMAX : 1); ++i) {
-                        if (xa + i >= xb) break;
-                        gather(xa + i);
-                    }
-                } else {
-                    for (int x = xa; x < xb; ++x) gather(x);
-                }
-                // this ring buffer may be refilled once every lane has read it
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0 && k + kRatAdjStages < rows) issue(k + kRatAdjStages);
-                // column sums: column c0 + lane collects tap l of the cell l lanes below
-                const float4 wy = yw[y - y0];
-                const float By[4] = {wy.x, wy.y, wy.z, wy.w};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float t1 = __shfl_up_sync(kFull, q4[1][c], 1);
-                    const float t2 = __shfl_up_sync(kFull, q4[2][c], 2);
-                    const float t3 = __shfl_up_sync(kFull, q4[3][c], 3);
-                    const float h = q4[0][c] + (lane >= 1 ? t1 : 0.f) + (lane >= 2 ? t2 : 0.f) + (lane >= 3 ? t3 : 0.f);
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) hy[m][c] = fmaf(By[m], h, hy[m][c]);
-                }
-            }
-            if (!ok) break;
-            const float4 wz = zw[z - z0];
-            const float Bz[4] = {wz.x, wz.y, wz.z, wz.w};
-#pragma unroll
-            for (int n = 0; n < 4; ++n)
+        for (int kz = kz0; ok && kz < kz1; ++kz) {
+            const int zb = imax(z0, cell_first(kz, d.num[2], d.den[2], d.off[2]));
+            const int ze = imin(z1, cell_first(kz + 1, d.num[2], d.den[2], d.off[2]));
+            for (int z = zb; ok && z < ze; ++z) {
+                float hy[4][3];
 #pragma unroll
                 for (int m = 0; m < 4; ++m)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) hz[n][m][c] = fmaf(Bz[n], hy[m][c], hz[n][m][c]);
+                    for (int c = 0; c < 3; ++c) hy[m][c] = 0.f;
+                for (int y = y0; y < y1; ++y, ++k) {
+                    const unsigned qq = q0 + (unsigned)k, st = qq % kRatAdjStages;
+                    if (!mbar_wait_bounded(bars + 2 * st, (qq / kRatAdjStages) & 1u)) {
+                        // a bulk copy never completed: record it, give the copies still in
+                        // flight a bounded chance to land, and stop this warp
+                        if (lane == 0) atomicOr(&g_err, kErrTimeout);
+                        for (int p = k + 1; p < rows && p < k + kRatAdjStages; ++p) {
+                            const unsigned qp = q0 + (unsigned)p;
+                            (void)mbar_wait_bounded(bars + 2 * (qp % kRatAdjStages), (qp / kRatAdjStages) & 1u);
+                        }
+                        ok = false;
+                        break;
+                    }
+                    const uintptr_t g = row_addr(k);
+                    unsigned char* sb = bufs + st * buf + (g & 15);
+                    if (g < A0 || g + (uintptr_t)nbytes > A1) {
+                        // first or last row of the array: its elements outside the bulk copy
+                        const RowLoad L = row_load(reinterpret_cast<const unsigned char*>(g), nbytes, A0, A1);
+                        for (int i = lane; i < nbytes / 4; i += 32) {
+                            const uintptr_t a = g + 4u * (uintptr_t)i;
+                            if (a < L.s0 || a >= L.s1) reinterpret_cast<float*>(sb)[i] = *reinterpret_cast<const float*>(a);
+                        }
+                    }
+                    __syncwarp();
+                    float q4[4][3];
+#pragma unroll
+                    for (int l = 0; l < 4; ++l)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) q4[l][c] = 0.f;
+                    // x-transpose of the lane's cell: q_l += B_l(x) G(x), voxels in order
+                    auto gather = [&](int x) {
+                        float B[4];
+                        if (TABLE) {
+                            const float4 w = xw[x];
+                            B[0] = w.x;
+                            B[1] = w.y;
+                            B[2] = w.z;
+                            B[3] = w.w;
+                        } else {
+                            axis_weights(x, col, d.num[0], d.den[0], d.off[0], B);
+                        }
+                        BSI_GUARD(x >= sx0 && (int)(g & 15) + 12 * (x - sx0) + 12 <= buf, kErrStage, &g_err) {
+                            const uint32_t sv = smem_u32(sb) + 12u * (uint32_t)(x - sx0);
+                            const float g0 = lds_f32(sv), g1 = lds_f32(sv + 4), g2 = lds_f32(sv + 8);
+#pragma unroll
+                            for (int l = 0; l < 4; ++l) {
+                                q4[l][0] = fmaf(B[l], g0, q4[l][0]);
+                                q4[l][1] = fmaf(B[l], g1, q4[l][1]);
+                                q4[l][2] = fmaf(B[l], g2, q4[l][2]);
+                            }
+                        }
+                    };
+                    if (CMAX > 0) {   // CMAX >= ceil(num / den) >= xb - xa: unrolled
+#pragma unroll
+                        for (int i = 0; i < (CMAX > 0 ? CMAX : 1); ++i) {
+                            if (xa + i >= xb) break;
+                            gather(xa + i);
+                        }
+                    } else {
+                        for (int x = xa; x < xb; ++x) gather(x);
+                    }
+                    // this ring buffer may be refilled once every lane has read it
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0 && k + kRatAdjStages < rows) issue(k + kRatAdjStages);
+                    // column sums: column c0 + lane collects tap l of the cell l lanes below
+                    const float4 wy = yw[y - y0];
+                    const float By[4] = {wy.x, wy.y, wy.z, wy.w};
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float t1 = __shfl_up_sync(kFull, q4[1][c], 1);
+                        const float t2 = __shfl_up_sync(kFull, q4[2][c], 2);
+                        const float t3 = __shfl_up_sync(kFull, q4[3][c], 3);
+                        const float h = q4[0][c] + (lane >= 1 ? t1 : 0.f) + (lane >= 2 ? t2 : 0.f) + (lane >= 3 ? t3 : 0.f);
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) hy[m][c] = fmaf(By[m], h, hy[m][c]);
+                    }
+                }
+                if (!ok) break;
+                const float4 wz = zw[z - z0];
+                const float Bz[4] = {wz.x, wz.y, wz.z, wz.w};
+#pragma unroll
+                for (int n = 0; n < 4; ++n)
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) hz[n][m][c] = fmaf(Bz[n], hy[m][c], hz[n][m][c]);
+            }
+            if (!ok) break;
+            // grid plane kz is complete for this unit: write it, roll the window by one plane
+            rat_flush_plane(P + (kz - kz0) * kRatPartPlane, hz[0], lane);
+#pragma unroll
+            for (int n = 0; n < 3; ++n)
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) hz[n][m][c] = hz[n + 1][m][c];
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) hz[3][m][c] = 0.f;
         }
         q = q0 + (unsigned)rows;
         if (!ok) break;
-        // the unit's partial sums: [plane n][row m][column lane][channel]
-        float* P = part + un * kRatPartFloats;
+        // planes kz1 .. kz1 + 2 get contributions from this unit's last cells only
 #pragma unroll
-        for (int n = 0; n < 4; ++n)
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                float* e = P + ((n * 4 + m) * 32 + lane) * 3;
-                e[0] = hz[n][m][0];
-                e[1] = hz[n][m][1];
-                e[2] = hz[n][m][2];
-            }
+        for (int n = 0; n < 3; ++n) rat_flush_plane(P + (kz1 - kz0 + n) * kRatPartPlane, hz[n], lane);
     }
     __syncwarp();
     if (lane == 0)
@@ -506,12 +533,12 @@ __global__ void __launch_bounds__(kRatAdjWarps * 32, 2)
 }
 
 // One thread per stored control point (gx, gy, gz): the units that cover it are
-// z-cells kz = gz - n (n = 0..3), every part of each, y-cells jy = gy - m, and
-// the strips xs whose 32 columns [xs sc, xs sc + 32) hold gx.
+// the z-chunks whose planes [kz0, kz0 + cells + 3) hold gz, y-cells jy = gy - m
+// (m = 0..3), and the strips xs whose 32 columns [xs sc, xs sc + 32) hold gx.
 __global__ void __launch_bounds__(256, 4)
     bsi_rational_adjoint_reduce_kernel(const __grid_constant__ RatDesc d, const float* __restrict__ part,
                                        float* __restrict__ dphi, int ncx, int ncy, int ncz, int nsx, int sc,
-                                       int zsplit) {
+                                       int zc) {
     (void)ncx;
     const long long npts = (long long)d.nx * d.ny * d.nz;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -520,16 +547,20 @@ __global__ void __launch_bounds__(256, 4)
         const long long t = p / d.nx;
         const int gy = (int)(t % d.ny), gz = (int)(t / d.ny);
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        for (int kz = imax(0, gz - 3); kz <= imin(gz, ncz - 1); ++kz)
-            for (int zp = 0; zp < zsplit; ++zp)
-                for (int jy = imax(0, gy - 3); jy <= imin(gy, ncy - 1); ++jy)
-                    for (int xs = imin(nsx - 1, gx / sc); xs >= 0 && gx - xs * sc < 32; --xs) {
-                        const long long un = (((long long)kz * zsplit + zp) * ncy + jy) * nsx + xs;
-                        const float* e = part + un * kRatPartFloats + (((gz - kz) * 4 + (gy - jy)) * 32 + (gx - xs * sc)) * 3;
-                        s0 += e[0];
-                        s1 += e[1];
-                        s2 += e[2];
-                    }
+        const int nch = (ncz + zc - 1) / zc;
+        for (int ch = imin(nch - 1, gz / zc); ch >= 0; --ch) {
+            const int pz = gz - ch * zc;                  // plane slot within the chunk
+            if (pz >= imin(zc, ncz - ch * zc) + 3) break;  // beyond the chunk's planes (and every earlier chunk's)
+            for (int jy = imax(0, gy - 3); jy <= imin(gy, ncy - 1); ++jy)
+                for (int xs = imin(nsx - 1, gx / sc); xs >= 0 && gx - xs * sc < 32; --xs) {
+                    const long long un = ((long long)ch * ncy + jy) * nsx + xs;
+                    const float* e = part + un * (long long)(zc + 3) * kRatPartPlane +
+                                     ((pz * 4 + (gy - jy)) * 32 + (gx - xs * sc)) * 3;
+                    s0 += e[0];
+                    s1 += e[1];
+                    s2 += e[2];
+                }
+        }
         dphi[3 * p] = s0;
         dphi[3 * p + 1] = s1;
         dphi[3 * p + 2] = s2;
@@ -546,11 +577,12 @@ RatAdjPlan rational_adjoint_plan(const RatDesc& d) {
     const int cmax = (d.num[0] + d.den[0] - 1) / d.den[0];
     pl.sc = imin(kGroupCells, kRatStripVox / cmax);
     pl.nsx = (int)cdiv(pl.ncx, pl.sc);
-    pl.zsplit = 1;
-    while (2 * pl.zsplit <= d.num[2] / d.den[2] &&
-           (long long)pl.ncz * pl.zsplit * pl.ncy * pl.nsx < kRatAdjMinUnits)
-        pl.zsplit *= 2;
-    pl.part_floats = (long long)pl.ncz * pl.zsplit * pl.ncy * pl.nsx * kRatPartFloats;
+    // a unit's planes (at most zc ceil(num_z / den_z)) fit the kernel's weight buffer
+    const int zmax = (d.num[2] + d.den[2] - 1) / d.den[2];
+    pl.zc = kRatAdjMaxZc;
+    while (pl.zc > 1 && (cdiv(pl.ncz, pl.zc) * pl.ncy * pl.nsx < kRatAdjMinUnits || pl.zc * zmax > kRatCellMax))
+        pl.zc /= 2;
+    pl.part_floats = cdiv(pl.ncz, pl.zc) * pl.ncy * pl.nsx * (pl.zc + 3) * kRatPartPlane;
     return pl;
 }
 
@@ -560,7 +592,8 @@ cudaError_t launch_adjoint_rational(const RatDesc& d, const float* grad, float* 
     const int cmax = (d.num[0] + d.den[0] - 1) / d.den[0];
     const bool table = d.X <= kRatTableMaxX;
     const int table_bytes = table ? 16 * d.X : 0;
-    const int per_warp = kRatAdjWarpBytes + 2 * kRatCellMax * 16;
+    const int buf = rat_adj_buf(pl.sc * cmax);   // a strip holds at most sc cells of cmax voxels
+    const int per_warp = rat_adj_warp_bytes(buf) + 2 * kRatCellMax * 16;
     int wpc = (kSmemBudget - table_bytes) / per_warp;
     wpc = wpc < 1 ? 1 : (wpc > kRatAdjWarps ? kRatAdjWarps : wpc);
     const int threads = wpc * 32, smem = wpc * per_warp + table_bytes;
@@ -575,15 +608,15 @@ cudaError_t launch_adjoint_rational(const RatDesc& d, const float* grad, float* 
     KernelFacts f;
     cudaError_t e = kernel_facts(kern, threads, smem, &f);
     if (e != cudaSuccess) return e;
-    const long long units = pl.part_floats / kRatPartFloats;
+    const long long units = pl.part_floats / ((pl.zc + 3) * kRatPartPlane);
     const long long want = cdiv(units, wpc);
     const long long cap = (long long)f.sms * f.ctas_per_sm;
     const int grid = (int)(want < cap ? want : cap);
     if (grid > 0) {
-        int ncx = pl.ncx, ncy = pl.ncy, ncz = pl.ncz, nsx = pl.nsx, sc = pl.sc, zsplit = pl.zsplit;
+        int ncx = pl.ncx, ncy = pl.ncy, ncz = pl.ncz, nsx = pl.nsx, sc = pl.sc, zc = pl.zc, bufb = buf;
         const float* gptr = grad;
         void* args[] = {const_cast<RatDesc*>(&d), (void*)&gptr, (void*)&part, (void*)&ncx, (void*)&ncy,
-                        (void*)&ncz, (void*)&nsx, (void*)&sc, (void*)&zsplit};
+                        (void*)&ncz, (void*)&nsx, (void*)&sc, (void*)&zc, (void*)&bufb};
         e = cudaLaunchKernel(kern, dim3(grid), dim3(threads), args, (size_t)smem, s);
         if (e != cudaSuccess) return e;
     }
@@ -592,7 +625,7 @@ cudaError_t launch_adjoint_rational(const RatDesc& d, const float* grad, float* 
     const int rg = (int)(rgrid < 4LL * f.sms * 8 ? rgrid : 4LL * f.sms * 8);
     if (rg > 0)
         bsi_rational_adjoint_reduce_kernel<<<rg, 256, 0, s>>>(d, part, dphi, pl.ncx, pl.ncy, pl.ncz, pl.nsx, pl.sc,
-                                                              pl.zsplit);
+                                                              pl.zc);
     return cudaGetLastError();
 }
 

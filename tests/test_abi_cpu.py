@@ -273,9 +273,10 @@ def test_rational_geometry_and_validation_before_cuda(lib):
 
 
 def test_rational_adjoint_workspace_and_validation_before_cuda(lib):
-    """The adjoint's workspace is 6 KB per unit (z-cell part x y-cell x strip of
-    up to 29 x-cells; z-cells split while there are fewer than 2048 units), and
-    the argument checks come before any CUDA call."""
+    """The adjoint's workspace: per unit (zc z-cells x one y-cell x a strip of up
+    to 29 x-cells) zc + 3 grid planes of 4 rows x 32 columns x 3 floats; zc = 4,
+    halved while there are fewer than 6000 units or a unit has more than 64
+    voxel planes.  The argument checks come before any CUDA call."""
     fake = 0x7F0000000000  # never dereferenced: validation fails first
     cases = [((300, 512, 512), (47, 47, 47), (10, 10, 10), (3, 0, 9)),
              ((7, 9, 11), (5, 7, 9), (2, 2, 2), (0, 3, 1)),
@@ -286,10 +287,10 @@ def test_rational_adjoint_workspace_and_validation_before_cuda(lib):
         cmax = -(-num[2] // den[2])
         sc = min(29, 232 // cmax)
         nsx = -(-ncell[2] // sc)
-        zsplit = 1
-        while 2 * zsplit <= num[0] // den[0] and ncell[0] * zsplit * ncell[1] * nsx < 2048:
-            zsplit *= 2
-        want = ncell[0] * zsplit * ncell[1] * nsx * 4 * 4 * 32 * 3 * 4
+        zc, zmax = 4, -(-num[0] // den[0])
+        while zc > 1 and (-(-ncell[0] // zc) * ncell[1] * nsx < 6000 or zc * zmax > 64):
+            zc //= 2
+        want = -(-ncell[0] // zc) * ncell[1] * nsx * (zc + 3) * 4 * 32 * 3 * 4
         assert lib.bsi_rational_adjoint_workspace_bytes(ctypes.byref(g)) == want, (shape, num)
     g = B.make_geom_rational((7, 9, 11), (5, 7, 9), (2, 2, 2), (0, 3, 1))
     need = lib.bsi_rational_adjoint_workspace_bytes(ctypes.byref(g))
