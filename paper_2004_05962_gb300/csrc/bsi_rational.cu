@@ -5,24 +5,26 @@
 // voxel x: q = x den + off, f = floor(q / num), u = (q - f num) / num, computed
 // in integers exactly, u rounded once to FP32.
 //
-// Three kernels:
-// - bsi_rational_strip_kernel (x-spacing <= 8 voxels): the integer path's
-//   decomposition with cells of varying width.  A warp takes the voxels of one
+// Three forward kernels:
+// - bsi_rational_strip_kernel (x-cells of 4 to 8 voxels whose 29-cell strips
+//   are mostly full): the integer path's decomposition with cells of varying
+//   width.  A warp takes the voxels of one
 //   z-cell x one y-cell x a strip of 29 x-cells; lane = stored grid column,
 //   whose 4 x 4 control points it contracts over z and y in registers; the
 //   x stage gets the three neighbouring columns by shuffles, and each lane
 //   writes the (floor or ceil of num/den) voxels of its cell into a staging row
 //   that leaves by bulk copy.
-// - bsi_rational_window_kernel (wider x-cells, nx <= 1024): a warp takes a run
+// - bsi_rational_window_kernel (other x-spacings, nx <= 1024): a warp takes a run
 //   of rows of a plane; the lanes contract the grid over z into a ring of four
 //   grid rows and over y into a line of nx columns in shared memory, then walk
 //   the row voxel by voxel (consecutive lanes, consecutive voxels).
-// - bsi_rational_kernel (wider x-cells, nx > 1024): the same walk, one warp per
+// - bsi_rational_kernel (other x-spacings, nx > 1024): the same walk, one warp per
 //   row, the line built from the grid directly.  Each lane advances its cell
 //   and remainder by exact integer steps (32 den = a num + b), so there is no
 //   integer division per voxel.
 // All three sum in the same order (z, then y, then x; lowest tap first), so
-// they give bit-identical fields.
+// they give bit-identical fields.  The adjoint (two kernels, deterministic)
+// follows the strip kernel's decomposition; see its section below.
 #include "bsi_kernels.cuh"
 #include "bsi_launch.h"
 
@@ -537,9 +539,7 @@ __global__ void __launch_bounds__(kRatAdjWarps * 32, 2)
 // (m = 0..3), and the strips xs whose 32 columns [xs sc, xs sc + 32) hold gx.
 __global__ void __launch_bounds__(256, 4)
     bsi_rational_adjoint_reduce_kernel(const __grid_constant__ RatDesc d, const float* __restrict__ part,
-                                       float* __restrict__ dphi, int ncx, int ncy, int ncz, int nsx, int sc,
-                                       int zc) {
-    (void)ncx;
+                                       float* __restrict__ dphi, int ncy, int ncz, int nsx, int sc, int zc) {
     const long long npts = (long long)d.nx * d.ny * d.nz;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npts; p += stride) {
@@ -624,8 +624,7 @@ cudaError_t launch_adjoint_rational(const RatDesc& d, const float* grad, float* 
     const long long rgrid = cdiv(npts, 256);
     const int rg = (int)(rgrid < 4LL * f.sms * 8 ? rgrid : 4LL * f.sms * 8);
     if (rg > 0)
-        bsi_rational_adjoint_reduce_kernel<<<rg, 256, 0, s>>>(d, part, dphi, pl.ncx, pl.ncy, pl.ncz, pl.nsx, pl.sc,
-                                                              pl.zc);
+        bsi_rational_adjoint_reduce_kernel<<<rg, 256, 0, s>>>(d, part, dphi, pl.ncy, pl.ncz, pl.nsx, pl.sc, pl.zc);
     return cudaGetLastError();
 }
 
