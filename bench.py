@@ -271,6 +271,13 @@ def run_ours(args, ws, rank, local):
                 "algorithmic_bytes_per_launch": adj_bytes, "avg_launch_ms": round(adj_ms, 5),
                 "peak_kind": f"{peak_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)"}
 
+    # both kernels of the step, timed inside it (the dominant one is the roofline above)
+    roof["in_step"] = {
+        "forward": {"kernel": "bsi_forward_kernel", "ms": round(fwd_ms, 5), "gbs": round(fwd_gbs, 1),
+                    "frac": round(fwd_gbs / hbm_peak, 4), "algorithmic_bytes": fwd_bytes},
+        "adjoint": {"kernel": "bsi_field_adjoint (partials + reduce)", "ms": round(adj_ms, 5),
+                    "gbs": round(adj_gbs, 1), "frac": round(adj_gbs / hbm_peak, 4), "algorithmic_bytes": adj_bytes}}
+
     extras = {}
     if not args.no_extras:
         extras = run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_peak)
@@ -290,7 +297,15 @@ def run_ours(args, ws, rank, local):
     out.update(extras)
     if "e2e" not in out:
         out["e2e"] = None
-    return out
+
+    def gpu_fields():
+        """The step's FP32 field and its BF16 variant, for the oracle leg's error report."""
+        f32 = P.bsi_field_forward(phi, shape, spacing)
+        b16 = P.bsi_field_forward(phi, shape, spacing, out_dtype=torch.bfloat16)
+        torch.cuda.synchronize()
+        return f32, b16
+
+    return out, gpu_fields
 
 
 def time_fn(fn, s, iters, warm=3):
@@ -439,7 +454,8 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
         gbs = model.forward_bytes(big, sp) / t / 1e6
         sweep["x".join(str(v) for v in sp[::-1])] = {
             "gvox_s": round(512 ** 3 / t / 1e6, 2), "ms": round(t, 5), "gbs": round(gbs, 1),
-            "frac_of_hbm": round(gbs / hbm_peak, 4)}
+            "frac_of_copy_peak": round(gbs / hbm_peak, 4), "frac_of_write_probe": round(gbs / write_peak, 4),
+            "frac_of_nominal": round(gbs / 7900.0, 4)}
     res["sweep_512cubed_fwd"] = sweep
     del out
 
@@ -453,7 +469,7 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
         gbs = model.adjoint_bytes(big, sp) / t / 1e6
         sweep["x".join(str(v) for v in sp[::-1])] = {
             "gvox_s": round(512 ** 3 / t / 1e6, 2), "ms": round(t, 5), "gbs": round(gbs, 1),
-            "frac_of_hbm": round(gbs / hbm_peak, 4)}
+            "frac_of_copy_peak": round(gbs / hbm_peak, 4), "frac_of_nominal": round(gbs / 7900.0, 4)}
         del d_, w_
     res["sweep_512cubed_adj"] = sweep
     del g
@@ -473,12 +489,13 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
         P.bsi_field_forward_batched(phis, shapes, spacings, outs=outs)
         P.bsi_field_adjoint_batched(grads, spacings, outs=dps, workspace=bws)
 
-    # untuned (library defaults), then autotuned launch shapes per spacing class
+    # untuned (library defaults), then ONE launch shape tuned for the whole batch
+    # (timed in this run: the tuner's cache is bypassed)
     from paper_2004_05962_gb300 import tune
 
     t_default = time_fn(bstep, s, 10)
     t_tune0 = time.time()
-    tuned = tune.tune_batched(shapes, spacings, iters=5)
+    tuned = tune.tune_batched(shapes, spacings, iters=5, retune=True)
     tune_s = time.time() - t_tune0
     bws = torch.empty(P.bsi_batched_adjoint_workspace_bytes(shapes, spacings), dtype=torch.uint8, device=dev)
 
@@ -499,6 +516,7 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
                          "vs_single_volume_fwd_adj": round((bvox / tb) / (nvox / (ms + msa)), 3),
                          "launches_per_step": batch_launches(shapes, spacings), "cuda_graph": True,
                          "autotuned": {k: v for k, v in tuned.items() if k not in ("dx", "dy", "dz")},
+                         "autotuned_scope": "one launch shape for the whole batch, timed in this run",
                          "spacing_classes": len(set(map(tuple, spacings))),
                          "tuning_s": round(tune_s, 1), "gvox_s_fwd_adj_untuned": round(bvox / t_default / 1e6, 2)}
     P.bsi_set_tile_configs([])
@@ -555,8 +573,36 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
     h2d = phi_h.numel() * 4 + grad_h.numel() * 4
     d2h = dphi_h[0].numel() * 4
     assert torch.equal(dphi_h[1].to(dev), P.bsi_field_adjoint(grad, spacing, workspace=work))
+    # the host link's own rates, the e2e denominator: one pinned copy of the
+    # step's largest input (the voxel gradient) host -> device and back, each
+    # timed alone on a copy stream, best of 5
+    back_h = torch.empty(grad.shape, dtype=grad.dtype).pin_memory()
+
+    def copy_ms(fn, st):
+        best = float("inf")
+        for _ in range(6):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(st)
+            with torch.cuda.stream(st):
+                fn()
+            b.record(st)
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+
+    nb = grad_h.numel() * 4
+    h2d_gbs = nb / copy_ms(lambda: grad_d[0].copy_(grad_h, non_blocking=True), s_up) / 1e6
+    d2h_gbs = nb / copy_ms(lambda: back_h.copy_(grad_d[0], non_blocking=True), s_down) / 1e6
+    # copies of one direction share a link direction; the two directions overlap
+    bound_ms = max(h2d / h2d_gbs, d2h / d2h_gbs) / 1e6
+    del back_h
     res["e2e"] = {"value": round(nvox / te / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                   "d2h_bytes_per_step": d2h, "ms_per_step": round(te, 4),
+                  "link": {"h2d_gbs": round(h2d_gbs, 1), "d2h_gbs": round(d2h_gbs, 1),
+                           "how": f"one pinned {nb / 1e6:.0f} MB copy each way, best of 6",
+                           "bound_gvox_s": round(nvox / bound_ms / 1e6, 3),
+                           "frac_of_link_bound": round(bound_ms / te, 4)},
                   "how": "pinned host inputs uploaded every step, dL/dphi read back every step, field kept on "
                          "the device; uploads / read-backs of neighbouring steps overlap the kernels (2 copy streams)"}
     return res
@@ -564,9 +610,13 @@ def run_extras(args, P, synth, model, dev, s, phi, grad, field, dphi, work, hbm_
 
 # ------------------------------------------------------------------ oracle legs
 
-def oracle_slab_rate(budget_s, shape=CT_SHAPE, spacing=CT_SPACING, seed=2):
+def oracle_slab_rate(budget_s, shape=CT_SHAPE, spacing=CT_SPACING, seed=2, gpu_fields=None):
     """Times the FP64 oracle (forward + adjoint, all host cores) on a z-slab of the
-    workload sized to ~budget_s seconds; returns (gvox_s, cores, sample text)."""
+    workload sized to ~budget_s seconds (planes [0, zs); the whole volume when it
+    fits); returns (gvox_s, cores, sample text, errors).  With ``gpu_fields`` (a
+    function returning the library's FP32 and BF16 fields of the same control
+    grid, on the device), ``errors`` holds their max / mean absolute error
+    against the oracle's forward over the timed planes (else None)."""
     import numpy as np
 
     import oracle
@@ -577,22 +627,47 @@ def oracle_slab_rate(budget_s, shape=CT_SHAPE, spacing=CT_SPACING, seed=2):
     phi = synth.gaussian_random_phi(shape, spacing, 3.0, 2.0, seed=seed)
     rng = np.random.default_rng(seed)
 
-    def run(zs):
+    def run(zs, keep=False):
         sub = (zs, Y, X)
         nzs = -(-zs // dz) + 3
         ph = np.ascontiguousarray(phi[:nzs])
         g = rng.standard_normal(sub + (3,), dtype=np.float32)
         t = time.perf_counter()
-        oracle.forward(ph, sub, spacing)
+        f = oracle.forward(ph, sub, spacing)
         oracle.adjoint(g, spacing)
-        return time.perf_counter() - t
+        return time.perf_counter() - t, (f if keep else None)
 
-    t1 = run(1)
+    t1, _ = run(1)
     zs = int(max(1, min(Z, budget_s / max(t1, 1e-6))))
-    t = run(zs)
+    t, want = run(zs, keep=gpu_fields is not None)
     vox = zs * Y * X
     cores = oracle.threads()
-    return vox / t / 1e9, cores, f"forward + adjoint of a {X}x{Y}x{zs} z-slab (of {Z}) of the same workload, {t:.1f} s"
+    sample = f"forward + adjoint of a {X}x{Y}x{zs} z-slab (of {Z}) of the same workload, {t:.1f} s"
+    errors = None
+    if gpu_fields is not None:
+        # planes [0, zs) of the whole volume's field need only grid planes
+        # [0, ceil(zs / dz) + 3): the slab's forward is the volume's, voxel for voxel
+        amax = float(np.abs(phi).max())
+        errors = {}
+        for name, dev_field in zip(("fwd_f32", "fwd_bf16"), gpu_fields()):
+            mx, tot, over = 0.0, 0.0, 0
+            for z0 in range(0, zs, 32):
+                z1 = min(zs, z0 + 32)
+                got = dev_field[z0:z1].float().cpu().numpy().astype(np.float64)
+                w = want[z0:z1]
+                d = np.abs(got - w)
+                mx = max(mx, float(d.max()))
+                tot += float(d.sum())
+                if name == "fwd_bf16":
+                    over += int(np.count_nonzero(d > 2.0 ** -8 * np.abs(w) + (1 + 2.0 ** -8) * 1e-5 * amax))
+                else:
+                    over += int(np.count_nonzero(d > 1e-5 * amax))
+            e = {"max_abs": mx, "mean_abs": tot / (3.0 * vox), "max_abs_over_max_phi": mx / amax,
+                 "voxels": vox, "beyond_bound": over}
+            e["bound"] = ("|err| <= 2^-8 |T| + (1 + 2^-8) 1e-5 max|phi| (RNE of the FP32 field)" if name == "fwd_bf16"
+                          else "|err| <= 1e-5 max|phi|")
+            errors[name] = e
+    return vox / t / 1e9, cores, sample, errors
 
 
 def run_reference(args, ws, rank):
@@ -754,12 +829,14 @@ def main():
     if args.section == "rational":
         print(json.dumps(run_section_rational(args)), flush=True)
         return
-    out = run_ours(args, ws, rank, local)
+    out, gpu_fields = run_ours(args, ws, rank, local)
     if rank == 0:
         if ws == 1 and not args.no_extras:
-            v, cores, sample = oracle_slab_rate(args.cpu_seconds)
+            v, cores, sample, errors = oracle_slab_rate(args.cpu_seconds, gpu_fields=gpu_fields)
             out["cpu_baseline"] = {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
                                    "sample": sample}
+            for name, e in (errors or {}).items():
+                out["components"][name]["err_vs_oracle"] = e
         print(json.dumps(out), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -95,7 +95,8 @@ bsi_status bsi_field_forward(const bsi_geom* g, const float* phi, void* field, b
                              bsi_stream_t stream);
 
 /* Workspace bytes bsi_field_adjoint needs for geometry g (0 for an empty
- * volume): the most any of its launch plans can use, since the tile-planes
+ * volume); no counterpart in the paper (its kernels have no adjoint): the
+ * most any of its launch plans can use, since the tile-planes
  * per warp unit are chosen per call (from the device's SM count) unless the
  * tile-config table fixes them. */
 size_t bsi_adjoint_workspace_bytes(const bsi_geom* g);
@@ -127,19 +128,25 @@ typedef struct {
 } bsi_instance;
 
 /* Batched forward over n volumes of uneven size and spacing (a registration
- * batch): one persistent launch walks the tiles of every volume; instances are
+ * batch); no counterpart in the paper, which interpolates one volume per call:
+ * Eq. 1 (Sec. 2.1) per instance.  One persistent launch walks the tiles of
+ * every volume; instances are
  * passed by value in the kernel parameters (up to 64 per launch, larger
  * batches are split), so no device copy of the descriptors is needed and the
  * call is capturable.  `inst` is host memory, read during the call only. */
 bsi_status bsi_field_forward_batched(const bsi_instance* inst, int n, bsi_dtype out_dtype,
                                      bsi_stream_t stream);
 
-/* Workspace bytes bsi_field_adjoint_batched needs for these n instances. */
+/* Workspace bytes bsi_field_adjoint_batched needs for these n instances (no
+ * counterpart in the paper): the sum of each instance's bound, 16-byte aligned
+ * per instance. */
 size_t bsi_batched_adjoint_workspace_bytes(const bsi_instance* inst, int n);
 
-/* Batched adjoint over n volumes: one persistent partial-sum launch over all
- * volumes' tiles, then one reduce launch; grad_phi of every instance is
- * overwritten. */
+/* Batched adjoint over n volumes (no counterpart in the paper): the transpose
+ * of Eq. 1 per instance, as bsi_field_adjoint.  One persistent partial-sum
+ * launch over all volumes' tiles, then one reduce launch; grad_phi of every
+ * instance is overwritten.  workspace: device, >= the query's bytes, 16-byte
+ * aligned; contents on entry ignored. */
 bsi_status bsi_field_adjoint_batched(const bsi_instance* inst, int n, void* workspace,
                                      size_t workspace_bytes, bsi_stream_t stream);
 
@@ -158,13 +165,20 @@ bsi_status bsi_field_adjoint_batched(const bsi_instance* inst, int n, void* work
  * rejected with BSI_ERR_SCRATCH_LIMIT before anything is enqueued (the
  * 512x512x300 volume at spacing 5 needs 44 to 69 MB depending on the plan).
  * The call allocates no device memory: no cudaMalloc, cudaFree or allocating
- * library routine.  Its first call on a device looks up the array's device
- * address (cudaGetSymbolAddress, once per device, with that device current),
- * so make that first call before any stream capture.
- * Every call uses the same array, which keeps the previous call's contents;
- * the first kernel writes every scratch entry the second one reads, so no
- * clearing is needed.  Calls that overlap on the GPU (different streams, or
- * other threads, without ordering between them) race on the array: order
+ * library routine.  A call made while `stream` is not being captured looks up
+ * the array's device address (cudaGetSymbolAddress, with the device current)
+ * and remembers it per device; a call made during capture uses the remembered
+ * address.  So make one call on each device before any stream capture, and
+ * after a cudaDeviceReset make one call outside capture again (the reset
+ * unloads the module and with it the array).
+ * Every call uses the same array, which keeps the previous call's contents.
+ * In a normal call the first kernel writes every scratch entry the second
+ * one reads, so no clearing is needed.  If a kernel's bounded wait for a bulk
+ * copy runs out, the warp that waited stops without writing its entries, and
+ * grad_phi may then hold sums that include the previous call's leftovers:
+ * bsi_check_device_status reports such a call (BSI_DEVICE_FLAG_TIMEOUT), and its
+ * result must not be used.  Calls that overlap on the GPU (different streams,
+ * or other threads, without ordering between them) race on the array: order
  * them on one stream or synchronise between them. */
 #define BSI_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 bsi_status bsi_field_adjoint_noalloc(const bsi_geom* g, const float* grad_field, float* grad_phi,
@@ -218,7 +232,7 @@ bsi_status bsi_check_device_status(bsi_stream_t stream, uint32_t* flags);
 int bsi_version(void);
 
 /* ------------------------------------------------------------------------
- * Non-integer, non-aligned spacing (Sec. 7 leaves control grids that are not
+ * Non-integer, non-aligned spacing (Sec. 8 leaves control grids that are not
  * aligned to the voxel grid to future work, noting the weights must then be
  * computed on the fly).  Per axis (x, y, z) the spacing is num/den voxels and
  * the lattice is shifted by off/den voxels: voxel x has
@@ -276,7 +290,7 @@ bsi_status bsi_field_adjoint_rational(const bsi_geom_rational* g, const float* g
                                       void* workspace, size_t workspace_bytes, bsi_stream_t stream);
 
 /* The paper's own GPU formulations of Eq. 1, for its accuracy comparison
- * (Sec. 5.3) and as a measured contrast to the separable kernel:
+ * (Sec. 5.4) and as a measured contrast to the separable kernel:
  *   BSI_VARIANT_SEPARABLE  bsi_field_forward's strip kernel (FP32 output)
  *   BSI_VARIANT_TT         thread per tile (Sec. 3.2): the 64-term sum of Eq. 1
  *                          per channel, the cell's control points in registers
@@ -293,7 +307,7 @@ bsi_status bsi_field_forward_variant(const bsi_geom* g, const float* phi, float*
                                      bsi_stream_t stream);
 
 /* Scalar BSI: Eq. 1 with one channel, for interpolating (zooming) an image
- * whose samples serve as the control points (Sec. 7 names image
+ * whose samples serve as the control points (Sec. 8 names image
  * interpolation as another use of the method).  The same kernels as
  * bsi_field_forward with a channel count of 1:
  *   out[z][y][x] = sum_{l,m,n} B_l(u) B_m(v) B_n(w) coeff[k+n][j+m][i+l]
@@ -311,7 +325,7 @@ bsi_status bsi_scalar_forward(const bsi_geom* g, const float* coeff, void* out, 
  * In FFD registration the dense field of Eq. 1 exists to resample the
  * floating image (Sec. 6: NiftyReg interpolates the coarse control grid into
  * the fine deformation field, then warps the floating image with it); the
- * paper proposes merging such steps with BSI (Sec. 7).  These calls never
+ * paper proposes merging such steps with BSI (Sec. 8).  These calls never
  * store the field: each voxel's displacement T(x) becomes the sample position
  *   p = x + T(x)   (voxel units; floating-image voxel i sits at coordinate i)
  * of the floating image F, read with the trilinear interpolant of F extended

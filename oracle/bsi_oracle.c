@@ -402,7 +402,7 @@ int bsi_oracle_adjoint_points(int64_t X, int64_t Y, int64_t Z, int dx, int dy, i
 /* Resampling of a floating image by the BSI displacement field.              */
 /*                                                                             */
 /* The step of FFD that follows BSI, which the paper proposes to merge with    */
-/* it (Sec. 7): the floating image F [fZ][fY][fX] is sampled at p = x + T(x),  */
+/* it (Sec. 8): the floating image F [fZ][fY][fX] is sampled at p = x + T(x),  */
 /* T from Eq. 1 at voxel x, in voxel units.  F~ below is the trilinear         */
 /* interpolant of F extended by zeros outside it: with i = floor(p_x),         */
 /* a = p_x - i (likewise j, b and k, c),                                       */
@@ -522,7 +522,7 @@ int bsi_oracle_resample_grad(int64_t X, int64_t Y, int64_t Z, int dx, int dy, in
 }
 
 /* ------------------------------------------------------------------------- */
-/* Non-integer, non-aligned spacing (the paper's future work, Sec. 7: grids   */
+/* Non-integer, non-aligned spacing (the paper's future work, Sec. 8: grids   */
 /* not aligned to the voxel grid, weights computed on the fly).               */
 /*                                                                             */
 /* Per axis the spacing is num/den voxels and the lattice is shifted by       */

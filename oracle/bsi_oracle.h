@@ -62,7 +62,7 @@ int bsi_oracle_adjoint_points(int64_t X, int64_t Y, int64_t Z, int dx, int dy, i
                               int64_t npts, double* out, int nthreads);
 
 /* Resampling of a floating image F [fZ][fY][fX] by the Eq. 1 displacement
- * (the FFD step that follows BSI; Sec. 7 proposes merging it with BSI):
+ * (the FFD step that follows BSI; Sec. 8 proposes merging it with BSI):
  *   warped[z][y][x] = F~(x + T_x, y + T_y, z + T_z),
  * F~ the trilinear interpolant of F extended by zeros outside the image, in
  * voxel units. */
@@ -79,7 +79,7 @@ int bsi_oracle_resample_grad(int64_t X, int64_t Y, int64_t Z, int dx, int dy, in
                              int64_t fX, int64_t fY, int64_t fZ, const void* dW, int dw_f32,
                              double* G, int nthreads);
 
-/* Non-integer, non-aligned spacing (Sec. 7's future work): per axis a spacing
+/* Non-integer, non-aligned spacing (Sec. 8's future work): per axis a spacing
  * of num/den voxels and a lattice shift of off/den voxels (0 <= off < num):
  * u_x = (x den + off) / num, cell floor(u_x), offset u_x - floor(u_x); grid
  * dims floor(((N-1) den + off) / num) + 4 per axis.  Arrays num, den, off are

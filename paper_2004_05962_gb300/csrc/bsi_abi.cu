@@ -1129,22 +1129,29 @@ constexpr size_t kNoAllocScratchBytes = BSI_NOALLOC_SCRATCH_BYTES;
 // device address that noalloc_scratch() looks up.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch on the current device, looked up once per
-// device (with that device current) and cached.
-static cudaError_t noalloc_scratch(void** out) {
+// Device address of g_noalloc_scratch on the current device.  Outside stream
+// capture it is looked up afresh on every call (cheap, and right again after a
+// cudaDeviceReset has reloaded the module) and remembered per device; during
+// capture the remembered address is used, so a first call per device must come
+// before any capture (BSI_ERR_CUDA otherwise).
+static cudaError_t noalloc_scratch(cudaStream_t s, void** out) {
     static std::mutex mu;
     static std::unordered_map<int, void*> addr;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(mu);
-    auto it = addr.find(dev);
-    if (it == addr.end()) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        it = addr.emplace(dev, p).first;
+        addr[dev] = p;
     }
+    auto it = addr.find(dev);
+    if (it == addr.end()) return cudaErrorStreamCaptureUnsupported;
     *out = it->second;
     return cudaSuccess;
 }
@@ -1166,7 +1173,7 @@ extern "C" bsi_status bsi_field_adjoint_noalloc(const bsi_geom* g, const float* 
     if (need > kNoAllocScratchBytes) return BSI_ERR_SCRATCH_LIMIT;
     void* scratch = nullptr;
     if (need > 0) {
-        const cudaError_t e = noalloc_scratch(&scratch);
+        const cudaError_t e = noalloc_scratch(reinterpret_cast<cudaStream_t>(stream), &scratch);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return adjoint_impl(&in, 1, scratch, kNoAllocScratchBytes, reinterpret_cast<cudaStream_t>(stream), true);

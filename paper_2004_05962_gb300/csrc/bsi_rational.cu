@@ -1,6 +1,6 @@
 // bsi_rational.cu -- Eq. 1 for control grids that are not aligned to the voxel
 // grid: per axis a spacing of num/den voxels and a lattice shift of off/den
-// voxels (the paper's future work, Sec. 7: such grids need the B-spline weights
+// voxels (the paper's future work, Sec. 8: such grids need the B-spline weights
 // computed on the fly instead of from look-up tables).  Cell and offset of
 // voxel x: q = x den + off, f = floor(q / num), u = (q - f num) / num, computed
 // in integers exactly, u rounded once to FP32.

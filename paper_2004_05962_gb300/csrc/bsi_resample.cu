@@ -1,5 +1,5 @@
 // bsi_resample.cu -- BSI fused with the resampling of a floating image (the
-// FFD step that follows BSI; Sec. 7 proposes merging it with BSI), and the
+// FFD step that follows BSI; Sec. 8 proposes merging it with BSI), and the
 // voxel gradient of that resampling for the adjoint.
 //
 // A warp walks the forward's strips (forward_unit's decomposition and z / y /

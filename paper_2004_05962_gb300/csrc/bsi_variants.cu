@@ -1,5 +1,5 @@
 // bsi_variants.cu -- the paper's own GPU formulations of Eq. 1, kept as an
-// option for its accuracy comparison (Sec. 5.3, Tables of the average
+// option for its accuracy comparison (Sec. 5.4, Tables of the average
 // absolute error against an FP64 reference) and as a measured contrast to the
 // separable strip kernel of bsi_forward.cu:
 //

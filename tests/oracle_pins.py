@@ -293,7 +293,7 @@ def pin_points_match_dense(lib):
 
 # ---------------------------------------------------------------- resampling
 # The floating image sampled at x + T(x), trilinear with zeros outside (the FFD
-# step after BSI that Sec. 7 proposes to merge with it), and its gradient.
+# step after BSI that Sec. 8 proposes to merge with it), and its gradient.
 
 RESAMPLE_CASES = [  # (shape, spacing, floating image shape): equal and unequal image sizes
     ((7, 9, 11), (2, 3, 4), (7, 9, 11)),
@@ -435,7 +435,7 @@ def pin_resample_backward_fd(lib):
 
 # ---------------------------------------------------------------- non-integer spacing
 # Spacing num/den and lattice shift off/den voxels per axis ((z, y, x) order):
-# u = (x den + off) / num (Sec. 7's grids not aligned to the voxel grid).
+# u = (x den + off) / num (Sec. 8's grids not aligned to the voxel grid).
 
 RATIONAL_CASES = [  # (shape, num, den, off)
     ((7, 9, 11), (5, 7, 9), (2, 2, 2), (0, 3, 1)),        # spacings 2.5, 3.5, 4.5

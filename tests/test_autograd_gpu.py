@@ -8,7 +8,7 @@ import torch.nn.functional as F
 import oracle
 import paper_2004_05962_gb300 as P
 from paper_2004_05962_gb300 import synth
-from gpu_util import dev
+from gpu_util import dev, full_adjoint_check
 
 pytestmark = pytest.mark.gpu
 
@@ -42,6 +42,49 @@ def test_linear_loss_gradient_is_adjoint():
     want = P.bsi_field_adjoint(W.contiguous(), spacing)
     torch.cuda.synchronize()
     assert torch.equal(phi.grad, want)
+
+
+def _config4_inputs():
+    """192x192x160 at spacing 5: phi ~ U[-2, 2], W ~ N(0, 1), an 8-blob image and
+    a target warped by a second smooth grid (the oracle's field of it)."""
+    shape, spacing = (160, 192, 192), (5, 5, 5)
+    phi_np = synth.uniform_phi(shape, spacing, -2, 2, seed=4)
+    W_np = synth.normal_field(shape, seed=4)
+    img_np = synth.blob_image(shape, seed=4)
+    phi_star = synth.uniform_phi(shape, spacing, -1.5, 1.5, seed=47)
+    tgt = warp(torch.from_numpy(img_np), torch.from_numpy(oracle.forward(phi_star, shape, spacing)).float())
+    return shape, spacing, phi_np, W_np, img_np, tgt
+
+
+def test_config4_linear_loss_gradient_vs_oracle_transpose():
+    """loss = sum(W * u) at 192x192x160, spacing 5: d loss / d phi is the
+    transpose of Eq. 1 applied to W; the autograd gradient is compared with the
+    oracle's transpose at every control point."""
+    shape, spacing, phi_np, W_np, _, _ = _config4_inputs()
+    phi = torch.from_numpy(phi_np).to(dev()).requires_grad_()
+    (torch.from_numpy(W_np).to(dev()) * P.field(phi, shape, spacing)).sum().backward()
+    torch.cuda.synchronize()
+    err = full_adjoint_check(W_np, spacing, phi.grad)
+    assert err.ok, err
+
+
+def test_config4_full_loss_gradient_vs_oracle_transpose():
+    """loss = sum(W * u) + SSD(warp(img, u), target) at 192x192x160, spacing 5:
+    dL/du (W plus the warp's gradient, from the harness's grid_sample) is captured
+    on its way into the adjoint, and the autograd gradient of phi is compared with
+    the oracle's transpose of it at every control point."""
+    shape, spacing, phi_np, W_np, img_np, tgt = _config4_inputs()
+    phi = torch.from_numpy(phi_np).to(dev()).requires_grad_()
+    u = P.field(phi, shape, spacing)
+    seen = {}
+    u.register_hook(lambda g: seen.setdefault("dLdu", g.detach().clone()))
+    L = loss_terms(u, torch.from_numpy(W_np).to(dev()), torch.from_numpy(img_np).to(dev()), tgt.to(dev()))
+    L.backward()
+    torch.cuda.synchronize()
+    dLdu = seen["dLdu"].cpu().numpy()
+    assert float(np.abs(dLdu - W_np).max()) > 1e-3   # the SSD term contributes
+    err = full_adjoint_check(dLdu, spacing, phi.grad)
+    assert err.ok, err
 
 
 def test_autograd_fd_fp64_32cubed():

@@ -1,5 +1,5 @@
 """The paper's thread-per-tile formulations (TT, TTLI) against the FP64 oracle,
-and the accuracy comparison of Sec. 5.3 (average absolute error of each GPU
+and the accuracy comparison of Sec. 5.4 (average absolute error of each GPU
 formulation with respect to an FP64 reference) on synthetic inputs."""
 import numpy as np
 import pytest
