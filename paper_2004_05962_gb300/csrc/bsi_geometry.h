@@ -228,12 +228,20 @@ BSI_HD int tma_block_rows(int dx, int dy) {
 }
 // Shared memory of one warp: 128 bytes of mbarriers, then the ring of stages.
 BSI_HD int tma_warp_smem(int stage_bytes, int stages) { return 128 + stages * stage_bytes; }
-// Default ring depth for a stage size: as deep as fits beside 12 warps, 2..3
-// (measured: a 4th stage slowed small blocks down; 3 beat 2 where both fit).
-constexpr int kTmaDefaultMaxStages = 3;
+// Default ring depth for a stage size, 2 or 3: 3 where it still fits beside
+// 12 warps (measured: a 4th stage slowed small blocks down; 3 beat 2 where
+// both fit), and also where two stages fall short of 12 warps anyway while
+// three keep at least 7.  Measured on the 512 x 512 x 300 volume at spacing 5
+// (9.7 KB stages: 11 warps x 2 stages or 7 warps x 3): equal alone, 11 us
+// faster right after a forward, whose field is still leaving L2 -- the deeper
+// ring rides out the longer load latency.  Where two stages reach 12 warps
+// (512^3 at spacing (4,5,6)) or three would leave 6 (spacing 8), fewer warps
+// cost 12-25% and the ring stays at 2.
+constexpr int kTmaMinDeepWarps = 7;
 BSI_HD int tma_default_stages(int stage_bytes) {
-    const int s = ((kTmaSmemBudget - 128) / kTmaMaxWarps - 128) / stage_bytes;
-    return s < kTmaMinStages ? kTmaMinStages : (s > kTmaDefaultMaxStages ? kTmaDefaultMaxStages : s);
+    const int w2 = (kTmaSmemBudget - 128) / tma_warp_smem(stage_bytes, 2);
+    const int w3 = (kTmaSmemBudget - 128) / tma_warp_smem(stage_bytes, 3);
+    return (w3 >= kTmaMaxWarps || (w2 < kTmaMaxWarps && w3 >= kTmaMinDeepWarps)) ? 3 : 2;
 }
 
 // Float index (x * 3 + channel) of the unit's first float and its 16-byte group.
