@@ -280,9 +280,13 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
                     // every lane stages all DX voxels of its tile, unpredicated: a cut or
                     // halo tile lands past the row end, inside the buffer (lane 31 ends at
                     // 32 DX voxels), and only [shift, shift + nbytes) is copied out
+                    // vector stores as wide as the row's alignment allows (a row 8 bytes
+                    // off a 16-byte boundary -- X even, X % 4 != 0 -- still takes 8-byte
+                    // stores at x-spacings 4 and 8)
                     constexpr int DXS = DX > 0 ? DX : 1;
                     constexpr int VW = BF16 ? 1 : tile_vec<DXS>();
-                    if (VW > 1 && (shift & (4 * VW - 1)) == 0) emit_tile<DXS, VW, BF16, C>(sv, p0, p1, p2, p3);
+                    if (VW == 4 && (shift & 15) == 0) emit_tile<DXS, 4, BF16, C>(sv, p0, p1, p2, p3);
+                    else if (VW >= 2 && (shift & 7) == 0) emit_tile<DXS, VW >= 2 ? 2 : 1, BF16, C>(sv, p0, p1, p2, p3);
                     else emit_tile<DXS, 1, BF16, C>(sv, p0, p1, p2, p3);
                 } else {
                     for (int r = 0; r < rn; ++r)
