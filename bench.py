@@ -174,17 +174,33 @@ def kernel_sources_sha():
 
 
 def ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
+    """DRAM bytes per launch of `kernel` from the committed ncu summary and
+    whether that capture was taken on the current kernel sources: (bytes, True),
+    (bytes of an older capture, False) or (None, False)."""
     p = ROOT / "profiles" / "dram_traffic.md"
     if not p.exists():
-        return None
+        return None, False
     sha = kernel_sources_sha()
+    old = None
     for line in p.read_text().splitlines():
         m = re.match(r"\|\s*(\S+)\s*\|\s*(\S+)\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9a-f]+)\s*\|", line)
-        if m and m.group(1) == kernel and m.group(4) == sha:
-            return float(m.group(3))
-    return None
+        if m and m.group(1) == kernel:
+            if m.group(4) == sha:
+                return float(m.group(3)), True
+            old = float(m.group(3))
+    return old, False
+
+
+def traffic_fields(kernels):
+    """roofline.traffic (summed over `kernels`, null unless every capture is on
+    the current sources) and a note that says which case applies."""
+    got = [ncu_traffic(k) for k in kernels]
+    if all(v is not None and fresh for v, fresh in got):
+        return sum(v for v, _ in got), "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, profiles/dram_traffic.md"
+    if all(v is not None for v, _ in got):
+        return None, ("stale: the committed ncu capture (%.0f B) predates the current kernel sources %s"
+                      % (sum(v for v, _ in got), kernel_sources_sha()))
+    return None, "no ncu capture committed for these kernels"
 
 
 # ------------------------------------------------------------------ our arm
@@ -229,24 +245,35 @@ def run_ours(args, ws, rank, local):
     clk = ClockSampler(local)
     clk.start()
     time.sleep(0.3)
-    barrier(ws)
-    torch.cuda.synchronize()
+
+    def timed(with_events):
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for k in range(args.steps):
+            step(evs[k] if with_events else None)
+        e1.record(s)
+        torch.cuda.synchronize()
+        barrier(ws)
+        return max_over_ranks(e0.elapsed_time(e1), ws, dev)
+
+    # Timed region A, the throughput: K steps with nothing between the kernels,
+    # so each launch may be scheduled while the previous one drains
+    # (programmatic dependent launches).  Timed region B, the per-kernel split
+    # the roofline reports: the same K steps with an event between the forward
+    # and the adjoint -- an event between two kernels forgoes that overlap, so
+    # B's steps run slower than A's.
     t0 = time.time()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(s)
-    for k in range(args.steps):
-        step(evs[k])
-    e1.record(s)
-    torch.cuda.synchronize()
-    barrier(ws)
+    ms_total = timed(False)
+    ms_total_b = timed(True)
     t1 = time.time()
     clk.stop()
-    ms_total = max_over_ranks(e0.elapsed_time(e1), ws, dev)
     ms_step = ms_total / args.steps
     fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     adj_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
     value = ws * nvox / (ms_step * 1e-3) / 1e9
-    launches = 3 * args.steps  # forward, adjoint partials, adjoint reduce per step
+    launches = 3 * args.steps  # forward, adjoint partials, adjoint reduce per step (timed region A)
 
     hbm_peak, peak_kind = measured_peaks()
     fwd_bytes = model.forward_bytes(shape, spacing)
@@ -255,23 +282,26 @@ def run_ours(args, ws, rank, local):
     adj_gbs = adj_bytes / (adj_ms * 1e-3) / 1e9
     dominant = "bsi_forward_kernel" if fwd_ms >= adj_ms else "bsi_field_adjoint (partials + reduce)"
     if fwd_ms >= adj_ms:
+        tr, note = traffic_fields(["bsi_forward_kernel"])
         roof = {"kernel": "bsi_forward_kernel", "bound": "hbm", "achieved": round(fwd_gbs, 1),
                 "peak": hbm_peak, "unit": "GB/s", "frac": round(fwd_gbs / hbm_peak, 4),
-                "traffic": ncu_traffic("bsi_forward_kernel"),
+                "traffic": tr, "traffic_note": note,
                 "algorithmic_bytes_per_launch": fwd_bytes, "avg_launch_ms": round(fwd_ms, 5),
                 "peak_kind": f"{peak_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)"}
     else:
         # X % 4 == 0 and dx <= 8: the adjoint's tensor-copy partials kernel runs
         pk = "bsi_adjoint_partials_tma_kernel" if shape[2] % 4 == 0 and spacing[2] <= 8 else \
             "bsi_adjoint_partials_kernel"
-        tp, tr = ncu_traffic(pk), ncu_traffic("bsi_adjoint_reduce_kernel")
+        tr, note = traffic_fields([pk, "bsi_adjoint_reduce_kernel"])
         roof = {"kernel": f"{pk} + bsi_adjoint_reduce_kernel (one bsi_field_adjoint call)",
                 "bound": "hbm", "achieved": round(adj_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(adj_gbs / hbm_peak, 4), "traffic": (tp + tr) if tp and tr else None,
+                "frac": round(adj_gbs / hbm_peak, 4), "traffic": tr, "traffic_note": note,
                 "algorithmic_bytes_per_launch": adj_bytes, "avg_launch_ms": round(adj_ms, 5),
                 "peak_kind": f"{peak_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)"}
 
     # both kernels of the step, timed inside it (the dominant one is the roofline above)
+    roof["in_step_how"] = ("CUDA events between the kernels over %d steps (timed region B: %.5f ms per step; "
+                           "region A without the events: %.5f ms)" % (args.steps, ms_total_b / args.steps, ms_step))
     roof["in_step"] = {
         "forward": {"kernel": "bsi_forward_kernel", "ms": round(fwd_ms, 5), "gbs": round(fwd_gbs, 1),
                     "frac": round(fwd_gbs / hbm_peak, 4), "algorithmic_bytes": fwd_bytes},
