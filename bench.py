@@ -396,7 +396,9 @@ def measure_resample(P, synth, model, dev, s, phi, field, dphi, hbm_peak, iters)
         "fwd_algorithmic_bytes": rb,
         "bwd_ms": round(ms_rsb, 5), "bwd_gvox_s": round(nvox / ms_rsb / 1e6, 2),
         "bwd_gbs_algorithmic": round(rbb / ms_rsb / 1e6, 1),
+        # the algorithmic bytes plus the voxel gradient G, written and read back once
         "bwd_bytes_moved": rbb + 24 * nvox,
+        "bwd_bytes_moved_over_algorithmic": round((rbb + 24 * nvox) / rbb, 3),
         "unfused_field_plus_torch_grid_sample_ms": round(ms_unf, 5),
         "unfused_max_abs_diff": agree,
         "image": "sum of 8 Gaussian blobs (sigma 8-20 voxels), seed 6; phi = the bench's CT control grid"}

@@ -100,7 +100,8 @@ def resample_bytes(shape, spacing, fshape=None, out_bytes=4):
 
 def resample_backward_bytes(shape, spacing, fshape=None):
     """Algorithmic bytes of its gradient with respect to phi: the floating image
-    and dL/dwarped read once, dL/dphi written once (the voxel gradient G that the
-    implementation passes from its first stage to the adjoint is extra)."""
+    and dL/dwarped read once, the control grid read and dL/dphi written once
+    (the voxel gradient G that the implementation passes from its first stage
+    to the adjoint is extra)."""
     fshape = shape if fshape is None else fshape
-    return 4 * math.prod(fshape) + 4 * math.prod(shape) + 12 * grid_points(shape, spacing)
+    return 4 * math.prod(fshape) + 4 * math.prod(shape) + 24 * grid_points(shape, spacing)
