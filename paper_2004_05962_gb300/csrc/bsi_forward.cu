@@ -11,6 +11,10 @@ static __device__ unsigned g_err;
 // a CTA take neighbouring units).  The per-unit work is near-uniform,
 // so the static assignment balances without an atomic ticket and is
 // deterministic.
+// Batched launches pack every spacing's arithmetic (see fwd_packed): their
+// narrow volumes fill 63% of the lanes, so the per-row instructions bound them.
+constexpr bool kBatchFwdPacked = true;
+
 template <int MAXB, bool BF16, bool GENERIC, int C = 3>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
     bsi_forward_kernel(const __grid_constant__ Batch<MAXB> b) {
@@ -19,6 +23,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
     const int warp = threadIdx.x >> 5;
     unsigned char* stage = smem + (size_t)warp * fwd_warp_smem(b.buf_bytes);
     const int wpc = blockDim.x >> 5;
+    constexpr bool PA = MAXB > 1 && kBatchFwdPacked;
     int ii = 0;
     int ring = 0;  // next staging buffer of the warp's store ring
     asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous kernel's writes are visible
@@ -29,17 +34,17 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
         const InstDesc& d = b.inst[ii];
         const long long ul = uu - d.unit_begin;
         if (GENERIC) {
-            forward_unit<0, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err);
+            forward_unit<0, BF16, C, PA>(d, ul, stage, b.buf_bytes, lane, ring, &g_err);
         } else {
             switch (d.dx) {
-                case 1: forward_unit<1, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
-                case 2: forward_unit<2, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
-                case 3: forward_unit<3, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
-                case 4: forward_unit<4, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
-                case 5: forward_unit<5, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
-                case 6: forward_unit<6, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
-                case 7: forward_unit<7, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
-                default: forward_unit<8, BF16, C>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 1: forward_unit<1, BF16, C, PA>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 2: forward_unit<2, BF16, C, PA>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 3: forward_unit<3, BF16, C, PA>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 4: forward_unit<4, BF16, C, PA>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 5: forward_unit<5, BF16, C, PA>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 6: forward_unit<6, BF16, C, PA>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                case 7: forward_unit<7, BF16, C, PA>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
+                default: forward_unit<8, BF16, C, PA>(d, ul, stage, b.buf_bytes, lane, ring, &g_err); break;
             }
         }
     }

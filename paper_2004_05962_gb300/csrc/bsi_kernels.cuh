@@ -244,12 +244,12 @@ __device__ __forceinline__ void emit_tile(uint32_t sv, const float (&p0)[C], con
 // buffer in its store ring (0 .. kStoreStages - 1).  C channels per control
 // point and voxel: 3 (the displacement field) or 1 (scalar interpolation,
 // layouts [nz][ny][nx] and [Z][Y][X]).
-template <int DX, bool BF16, int C = 3>
+template <int DX, bool BF16, int C = 3, bool PACK_ALL = false>
 __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, unsigned char* stage,
                                              int buf_bytes, int lane, int& ring, unsigned* err) {
     static_assert(C == 1 || C == 3, "one (scalar) or three (displacement) channels");
     constexpr int ES = BF16 ? 2 : 4;
-    constexpr bool PK = fwd_packed<DX, BF16>();
+    constexpr bool PK = PACK_ALL || fwd_packed<DX, BF16>();
     const int dx = DX > 0 ? DX : d.dx;
     const FwdUnit u = fwd_unit(d, ul);
     const int col = u.cell0 + lane;
@@ -363,9 +363,9 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
                     // stores at x-spacings 4 and 8)
                     constexpr int DXS = DX > 0 ? DX : 1;
                     constexpr int VW = BF16 ? 1 : tile_vec<DXS>();
-                    if (VW == 4 && (shift & 15) == 0) emit_tile<DXS, 4, BF16, C>(sv, p0, p1, p2, p3);
-                    else if (VW >= 2 && (shift & 7) == 0) emit_tile<DXS, VW >= 2 ? 2 : 1, BF16, C>(sv, p0, p1, p2, p3);
-                    else emit_tile<DXS, 1, BF16, C>(sv, p0, p1, p2, p3);
+                    if (VW == 4 && (shift & 15) == 0) emit_tile<DXS, 4, BF16, C, PK>(sv, p0, p1, p2, p3);
+                    else if (VW >= 2 && (shift & 7) == 0) emit_tile<DXS, VW >= 2 ? 2 : 1, BF16, C, PK>(sv, p0, p1, p2, p3);
+                    else emit_tile<DXS, 1, BF16, C, PK>(sv, p0, p1, p2, p3);
                 } else {
                     for (int r = 0; r < rn; ++r)
                         emit_voxel<BF16, C, PK>(sv + C * ES * r, wxb + 4 * r, p0, p1, p2, p3);

@@ -118,6 +118,13 @@ __global__ void __launch_bounds__(kRatWarps * 32) bsi_rational_kernel(const __gr
 
 // ---------------------------------------------------------------- strip kernel
 
+// The strip kernel takes channels 0 and 1 through packed FP32x2 arithmetic
+// (combine4; bitwise the scalar results): 2% faster at spacings 4.7 and 6.5 on
+// a 512 x 512 x 300 volume.  The adjoint stays scalar: packed, it ran 1.4-2.6%
+// slower there.
+constexpr bool kRatFwdPacked = true;
+constexpr bool kRatAdjPacked = false;
+
 constexpr int kRatStripMaxCell = 8;                            // voxels per x-cell (ceil(num/den)) it takes
 constexpr int kRatStripMinCell = 4;                            // x-spacing num/den it takes, at least
 constexpr int kRatStripVox = kGroupCells * kRatStripMaxCell;   // voxels of one staged row segment
@@ -227,16 +234,14 @@ __global__ void __launch_bounds__(kRatStripWarps * 32, 2)
             float pz[4][3];
 #pragma unroll
             for (int m = 0; m < 4; ++m)
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    pz[m][c] = fmaf(Bz[3], ph[3][m][c], fmaf(Bz[2], ph[2][m][c], fmaf(Bz[1], ph[1][m][c], Bz[0] * ph[0][m][c])));
+                combine4<3, kRatFwdPacked>(pz[m], Bz[0], Bz[1], Bz[2], Bz[3], ph[0][m], ph[1][m], ph[2][m], ph[3][m]);
             for (int y = y0; y < y1; ++y) {
                 const float4 wy = yw[y - y0];
                 const float By[4] = {wy.x, wy.y, wy.z, wy.w};
                 float p0[3], p1[3], p2[3], p3[3];
+                combine4<3, kRatFwdPacked>(p0, By[0], By[1], By[2], By[3], pz[0], pz[1], pz[2], pz[3]);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    p0[c] = fmaf(By[3], pz[3][c], fmaf(By[2], pz[2][c], fmaf(By[1], pz[1][c], By[0] * pz[0][c])));
                     p1[c] = __shfl_down_sync(kFull, p0[c], 1);
                     p2[c] = __shfl_down_sync(kFull, p0[c], 2);
                     p3[c] = __shfl_down_sync(kFull, p0[c], 3);
@@ -263,9 +268,10 @@ __global__ void __launch_bounds__(kRatStripWarps * 32, 2)
                     }
                     BSI_GUARD(shift + 12 * (x - sx0) + 12 <= kRatStripBuf && x >= sx0, kErrStage, &g_err) {
                         const uint32_t sv = smem_u32(sb) + 12u * (uint32_t)(x - sx0);
+                        float v[3];
+                        combine4<3, kRatFwdPacked>(v, B[0], B[1], B[2], B[3], p0, p1, p2, p3);
 #pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            sts_f32(sv + 4 * c, fmaf(B[3], p3[c], fmaf(B[2], p2[c], fmaf(B[1], p1[c], B[0] * p0[c]))));
+                        for (int c = 0; c < 3; ++c) sts_f32(sv + 4 * c, v[c]);
                     }
                 }
                 fence_proxy_async_smem();   // this lane's staging writes before the bulk copy reads them
@@ -466,11 +472,7 @@ __global__ void __launch_bounds__(kRatAdjWarps * 32, 2)
                             const uint32_t sv = smem_u32(sb) + 12u * (uint32_t)(x - sx0);
                             const float g0 = lds_f32(sv), g1 = lds_f32(sv + 4), g2 = lds_f32(sv + 8);
 #pragma unroll
-                            for (int l = 0; l < 4; ++l) {
-                                q4[l][0] = fmaf(B[l], g0, q4[l][0]);
-                                q4[l][1] = fmaf(B[l], g1, q4[l][1]);
-                                q4[l][2] = fmaf(B[l], g2, q4[l][2]);
-                            }
+                            for (int l = 0; l < 4; ++l) fma3_sel<kRatAdjPacked>(q4[l], B[l], g0, g1, g2);
                         }
                     };
                     if (CMAX > 0) {   // CMAX >= ceil(num / den) >= xb - xa: unrolled
@@ -489,15 +491,16 @@ __global__ void __launch_bounds__(kRatAdjWarps * 32, 2)
                     // column sums: column c0 + lane collects tap l of the cell l lanes below
                     const float4 wy = yw[y - y0];
                     const float By[4] = {wy.x, wy.y, wy.z, wy.w};
+                    float h[3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         const float t1 = __shfl_up_sync(kFull, q4[1][c], 1);
                         const float t2 = __shfl_up_sync(kFull, q4[2][c], 2);
                         const float t3 = __shfl_up_sync(kFull, q4[3][c], 3);
-                        const float h = q4[0][c] + (lane >= 1 ? t1 : 0.f) + (lane >= 2 ? t2 : 0.f) + (lane >= 3 ? t3 : 0.f);
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) hy[m][c] = fmaf(By[m], h, hy[m][c]);
+                        h[c] = q4[0][c] + (lane >= 1 ? t1 : 0.f) + (lane >= 2 ? t2 : 0.f) + (lane >= 3 ? t3 : 0.f);
                     }
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) fma3_sel<kRatAdjPacked>(hy[m], By[m], h[0], h[1], h[2]);
                 }
                 if (!ok) break;
                 const float4 wz = zw[z - z0];
@@ -505,9 +508,7 @@ __global__ void __launch_bounds__(kRatAdjWarps * 32, 2)
 #pragma unroll
                 for (int n = 0; n < 4; ++n)
 #pragma unroll
-                    for (int m = 0; m < 4; ++m)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) hz[n][m][c] = fmaf(Bz[n], hy[m][c], hz[n][m][c]);
+                    for (int m = 0; m < 4; ++m) fma3_sel<kRatAdjPacked>(hz[n][m], Bz[n], hy[m][0], hy[m][1], hy[m][2]);
             }
             if (!ok) break;
             // grid plane kz is complete for this unit: write it, roll the window by one plane
