@@ -158,22 +158,30 @@ __global__ void __launch_bounds__(256)
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
         if (d.nzc > 0) {
             // The covering partials: at most two tile-plane chunks (zc_hi - 1, zc_hi)
-            // times four tile-rows.  All 8 x 3 loads are issued before any sum, and
-            // the sum runs in the fixed order (chunk, row).
+            // times four tile-rows.  Their offsets differ by constants of the
+            // instance: e(t, m) = e(0, 0) + t sz - m sy (part_elem written out),
+            // so one 64-bit offset per point and adds give all eight.  All 8 x 3
+            // loads are issued before any sum, and the sum runs in the fixed
+            // order (chunk, row); channels 0 and 1 are added as packed pairs
+            // (bitwise the scalar sums).
             const int zc_hi = imin(d.nzc - 1, gz / d.zchunk);
+            const long long uf = adj_unit_floats(d);
+            const long long sy = (long long)d.nxg * uf - (long long)kGroupCells * 3;       // one tile-row less
+            const long long sz = (long long)d.ncy * d.nxg * uf - (long long)d.zchunk * 4 * kGroupCells * 3;  // next chunk
+            const int zc0 = zc_hi - 1, pz0 = gz - zc0 * d.zchunk;
+            const long long e00 = d.part_off + (((long long)zc0 * d.ncy + gy) * d.nxg + xg) * uf +
+                                  ((long long)pz0 * 4 * kGroupCells + j) * 3;
             float v[2][4][3];
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
-                const int zc = zc_hi - 1 + t;
-                const int pz = gz - zc * d.zchunk;
-                const bool zok = zc >= 0 && pz < imin(d.zchunk, d.ncz - zc * d.zchunk) + kHalo;
+                const int zc = zc0 + t;
+                const bool zok = zc >= 0 && pz0 - t * d.zchunk < imin(d.zchunk, d.ncz - zc * d.zchunk) + kHalo;
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     const int jy = gy - m;
                     v[t][m][0] = v[t][m][1] = v[t][m][2] = 0.f;
                     if (zok && jy >= 0 && jy < d.ncy) {
-                        const long long ul = ((long long)zc * d.ncy + jy) * d.nxg + xg;
-                        const long long e = part_elem(d, ul, pz, m, j);
+                        const long long e = e00 + t * sz - m * sy;
                         BSI_GUARD(e >= 0 && e + 3 <= ws_floats, kErrPartRead, &g_err) {
                             v[t][m][0] = __ldcs(part + e);
                             v[t][m][1] = __ldcs(part + e + 1);
@@ -182,14 +190,16 @@ __global__ void __launch_bounds__(256)
                     }
                 }
             }
+            float2 a = make_float2(s0, s1);
 #pragma unroll
             for (int t = 0; t < 2; ++t)
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
-                    s0 += v[t][m][0];
-                    s1 += v[t][m][1];
+                    a = __fadd2_rn(a, make_float2(v[t][m][0], v[t][m][1]));
                     s2 += v[t][m][2];
                 }
+            s0 = a.x;
+            s1 = a.y;
         }
         float* o = d.dphi + pl * 3;
         BSI_GUARD(pl >= 0 && pl < (long long)d.nx * d.ny * d.nz, kErrDphiWrite, &g_err) {
