@@ -70,6 +70,12 @@ struct Batch {
     InstDesc inst[MAXB];
 };
 
+// Index of instance i in a launch's descriptor array: the constant 0 when the
+// launch holds one instance (MAXB == 1), so that the descriptor's fields are
+// constant-bank operands rather than loads indexed by a register.
+template <int MAXB>
+BSI_HD int inst_index(int i) { return MAXB == 1 ? 0 : i; }
+
 BSI_HD long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
 BSI_HD int imin(int a, int b) { return a < b ? a : b; }
 BSI_HD int imax(int a, int b) { return a > b ? a : b; }
