@@ -371,6 +371,31 @@ static cudaError_t encode_grad_map(const InstDesc& d, CUtensorMap* m) {
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// The field of one instance as a 3-D tensor of 8-byte elements: (3 X ES / 8,
+// Y, Z), with a box of (the strip's bytes / 8, rb, 1) for the forward's
+// tensor stores (fwd_tma_rows).
+static cudaError_t encode_field_map(const InstDesc& d, bool bf16, int rb, CUtensorMap* m) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t es = bf16 ? 2 : 4;
+    const cuuint64_t row = (cuuint64_t)d.X * 3 * es;
+    const cuuint64_t dims[3] = {row / 8, (cuuint64_t)d.Y, (cuuint64_t)d.Z};
+    const cuuint64_t strides[2] = {row, row * (cuuint64_t)d.Y};
+    const cuuint32_t box[3] = {(cuuint32_t)(fwd_tma_row_bytes(d.gcells, d.dx, bf16) / 8), (cuuint32_t)rb, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, d.field, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Rows per block when a single-volume forward takes the tensor-store path, else 0.
+static int forward_tma_rows(const InstDesc& d, bool bf16, bool generic) {
+    if (generic || d.units <= 0 || (reinterpret_cast<uintptr_t>(d.field) & 15) != 0 || !tensor_map_encoder())
+        return 0;
+    return fwd_tma_rows(d.X, d.dx, d.dy, d.gcells, bf16);
+}
+
 enum class Op { Forward, AdjointPartials, AdjointReduce };
 
 template <int MAXB>
@@ -389,7 +414,15 @@ static cudaError_t run_group(const Group& g, Op op, bool bf16, float* part, long
     if (g.inst.size() == 1) {
         Batch<1> b;
         to_batch(g, b);
-        if (op == Op::Forward) return launch_forward(b, bf16, g.generic, s, nullptr);
+        if (op == Op::Forward) {
+            const int rb = forward_tma_rows(b.inst[0], bf16, g.generic);
+            if (rb > 0) {
+                CUtensorMap map;
+                const cudaError_t e = encode_field_map(b.inst[0], bf16, rb, &map);
+                if (e == cudaSuccess) return launch_forward_tma(b, bf16, map, rb, s, nullptr);
+            }
+            return launch_forward(b, bf16, g.generic, s, nullptr);
+        }
         if (op == Op::AdjointPartials) {
             if (g.tma) {
                 TmaMaps<1> maps;

@@ -95,6 +95,21 @@ __device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_
                  :: "l"(gdst), "r"(smem_u32(ssrc)), "r"(bytes), "l"(pol) : "memory");
 }
 
+// Tiled tensor store (TMA) of one box of a 3-D tensor map from shared memory
+// at ssrc (128-byte aligned) into global memory, in the current bulk group;
+// parts of the box outside the tensor are not written.  tmap is the generic
+// address of a CUtensorMap held in kernel parameter space; the innermost
+// coordinate c0 times the element size must be a multiple of 16 bytes and no
+// coordinate may be negative.  Lines marked first for eviction, as bulk_store.
+__device__ __forceinline__ void tensor_store_3d(const void* tmap, int c0, int c1, int c2, const void* ssrc) {
+    asm volatile(
+        "{\n\t.reg .b64 pol;\n\t"
+        "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+        "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group.L2::cache_hint"
+        " [%0, {%1, %2, %3}], [%4], pol;\n}"
+        :: "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(ssrc)) : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 
 // Waits until at most N of this thread's committed bulk groups still read shared memory.

@@ -83,6 +83,64 @@ cudaError_t launch_forward(const Batch<MAXB>& b, bool bf16, bool generic, cudaSt
     return generic ? launch_fwd_t<MAXB, false, true>(b, s, info) : launch_fwd_t<MAXB, false, false>(b, s, info);
 }
 
+// Forward on the tensor-store path (one volume; see fwd_tma_rows): the same
+// persistent unit walk as bsi_forward_kernel, rows leaving in blocks of rb.
+template <bool BF16>
+__global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
+    bsi_forward_tma_kernel(const __grid_constant__ Batch<1> b, const __grid_constant__ CUtensorMap map, int rb,
+                           int blk_bytes) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // 128-byte aligned base (the launch adds 128 bytes for it)
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    const int lane = threadIdx.x & (kLanes - 1);
+    const int warp = threadIdx.x >> 5;
+    unsigned char* stage = smem + (size_t)warp * fwd_tma_warp_smem(blk_bytes);
+    const int wpc = blockDim.x >> 5;
+    int ring = 0;
+    const InstDesc& d = b.inst[0];
+    asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous kernel's writes are visible
+    for (long long r = 0;; ++r) {
+        const long long ul = slot_unit(r, blockIdx.x, warp, gridDim.x, wpc, b.total_units, false);
+        if (ul < 0) break;
+        switch (d.dx) {
+            case 1: forward_unit_tma<1, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            case 2: forward_unit_tma<2, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            case 3: forward_unit_tma<3, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            case 4: forward_unit_tma<4, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            case 5: forward_unit_tma<5, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            case 6: forward_unit_tma<6, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            case 7: forward_unit_tma<7, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            default: forward_unit_tma<8, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+        }
+    }
+    // the blocks must outlive every tensor store that reads them
+    if (lane == 0) bulk_wait_all<0>();
+    __syncwarp();
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+cudaError_t launch_forward_tma(const Batch<1>& b, bool bf16, const CUtensorMap& map, int rb, cudaStream_t s,
+                               LaunchInfo* info) {
+    const InstDesc& d = b.inst[0];
+    const int blk_bytes = pad128(rb * fwd_tma_row_bytes(d.gcells, d.dx, bf16));
+    const int wsm = fwd_tma_warp_smem(blk_bytes);
+    const int wpc = warps_per_cta(wsm, b.warps_req);
+    const int threads = wpc * kLanes;
+    const int smem = wpc * wsm + 128;
+    const void* kern = bf16 ? reinterpret_cast<const void*>(bsi_forward_tma_kernel<true>)
+                            : reinterpret_cast<const void*>(bsi_forward_tma_kernel<false>);
+    KernelFacts f;
+    cudaError_t e = kernel_facts(kern, threads, smem, &f);
+    if (e != cudaSuccess) return e;
+    const long long want = cdiv(b.total_units, wpc);
+    const long long cap = (long long)f.sms * f.ctas_per_sm;
+    const int grid = (int)(want < cap ? want : cap);
+    if (info) *info = LaunchInfo{grid, threads, smem, f.ctas_per_sm};
+    if (grid <= 0) return cudaSuccess;
+    if (bf16) return launch_pdl(bsi_forward_tma_kernel<true>, grid, threads, smem, s, b, map, rb, blk_bytes);
+    return launch_pdl(bsi_forward_tma_kernel<false>, grid, threads, smem, s, b, map, rb, blk_bytes);
+}
+
 // Scalar (one-channel) interpolation of a single volume.
 cudaError_t launch_forward_scalar(const Batch<1>& b, bool bf16, bool generic, cudaStream_t s, LaunchInfo* info) {
     if (bf16)

@@ -384,6 +384,92 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
     }
 }
 
+// One forward unit on the tensor-store path (see fwd_tma_rows): the rows of the
+// unit's tile-row are staged rb at a time into a block of `stage`'s ring (row
+// pitch = the strip's bytes, every row on a 16-byte boundary), and each block
+// leaves as one tensor store at (strip start, first row, plane); rows and
+// columns past the volume's end are clipped by the copy.  Halo lanes (lane >=
+// gcells) stage into the warp's spare slot after the ring.  Three channels.
+template <int DX, bool BF16>
+__device__ __forceinline__ void forward_unit_tma(const InstDesc& d, const void* tmap, long long ul,
+                                                 unsigned char* stage, int blk_bytes, int rb, int lane, int& ring,
+                                                 unsigned* err) {
+    constexpr int C = 3, ES = BF16 ? 2 : 4;
+    constexpr bool PK = fwd_packed<DX, BF16>();
+    constexpr int VW = BF16 ? 1 : tile_vec<DX>();
+    const FwdUnit u = fwd_unit(d, ul);
+    const int col = u.cell0 + lane;
+    float ph[4][4][C];
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            float a = 0.f, b = 0.f, c = 0.f;
+            if (col < d.nx) {
+                const long long e = phi_elem(d, u.kz + n, u.jy + m, col);
+                BSI_GUARD(e >= 0 && e + 3 <= 3LL * d.nx * d.ny * d.nz, kErrPhiRead, err) {
+                    const float* p = d.phi + e;
+                    a = __ldg(p);
+                    b = __ldg(p + 1);
+                    c = __ldg(p + 2);
+                }
+            }
+            ph[n][m][0] = a;
+            ph[n][m][1] = b;
+            ph[n][m][2] = c;
+        }
+
+    const int z0 = u.kz * d.dz, zn = imin(d.dz, d.Z - z0);
+    const int y0 = u.jy * d.dy, yn = imin(d.dy, d.Y - y0);
+    const int wzb = weight_base(d.dz), wyb = weight_base(d.dy);
+    const int rowb = d.gcells * DX * C * ES;           // row pitch of a block: the strip's bytes
+    const int c0 = (u.x0 * C * ES) >> 3;               // strip start in 8-byte elements (even: 16-byte aligned)
+    // this lane's tile in row 0 of a block, or the spare slot for halo lanes
+    const uint32_t lane_off = lane < d.gcells ? (uint32_t)(lane * DX * C * ES) : (uint32_t)(kStoreStages * blk_bytes);
+    BSI_GUARD(rowb * rb <= blk_bytes && (u.x0 * C * ES) % 16 == 0, kErrStage, err) {}
+
+    for (int rz = 0; rz < zn; ++rz) {
+        const float a0 = c_lut.w[wzb + 4 * rz], a1 = c_lut.w[wzb + 4 * rz + 1];
+        const float a2 = c_lut.w[wzb + 4 * rz + 2], a3 = c_lut.w[wzb + 4 * rz + 3];
+        float pz[4][C];
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            combine4<C, PK>(pz[m], a0, a1, a2, a3, ph[0][m], ph[1][m], ph[2][m], ph[3][m]);
+
+        for (int yb = 0; yb < yn; yb += rb) {
+            unsigned char* blk = stage + ring * blk_bytes;
+            ring = ring == kStoreStages - 1 ? 0 : ring + 1;
+            // (the block is free: the store of the block kStoreStages - 1 earlier has read it)
+            const uint32_t sv0 = smem_u32(lane < d.gcells ? blk : stage) + lane_off;
+            const int rows = imin(rb, yn - yb);
+            for (int r = 0; r < rows; ++r) {
+                const int ry = yb + r;
+                const float b0 = c_lut.w[wyb + 4 * ry], b1 = c_lut.w[wyb + 4 * ry + 1];
+                const float b2 = c_lut.w[wyb + 4 * ry + 2], b3 = c_lut.w[wyb + 4 * ry + 3];
+                float p0[C], p1[C], p2[C], p3[C];
+                combine4<C, PK>(p0, b0, b1, b2, b3, pz[0], pz[1], pz[2], pz[3]);
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    p1[c] = __shfl_down_sync(kFull, p0[c], 1);
+                    p2[c] = __shfl_down_sync(kFull, p0[c], 2);
+                    p3[c] = __shfl_down_sync(kFull, p0[c], 3);
+                }
+                // halo lanes write the spare slot again for every row (never copied out)
+                const uint32_t sv = sv0 + (lane < d.gcells ? (uint32_t)(r * rowb) : 0u);
+                emit_tile<DX, VW, BF16, C, PK>(sv, p0, p1, p2, p3);
+            }
+            fence_proxy_async_smem();  // this lane's staging writes before the tensor store reads them
+            __syncwarp();
+            if (lane == 0) {
+                tensor_store_3d(tmap, c0, y0 + yb, z0 + rz, blk);
+                bulk_commit();
+                bulk_wait_read<kStoreStages - 1>();
+            }
+            __syncwarp();  // lane 0's ring wait precedes every lane's next staging write
+        }
+    }
+}
+
 // ------------------------------------------------------------------ adjoint
 
 // Writes one completed grid plane of a unit's partial sums (lanes 3..31 hold

@@ -51,6 +51,32 @@ def test_forward_config_64cubed_seed1():
     assert err <= tol
 
 
+# Volumes whose rows leave by tensor stores in blocks of rows (16-byte rows and
+# strips; FP32 at x-spacings <= 4, BF16 at even x-spacings with X % 8 == 0): one
+# to eight rows per block, ragged tails in x (a short last strip), y (a last
+# tile-row inside the volume shorter than the block) and z.
+TENSOR_STORE = [
+    ((7, 13, 64), (2, 3, 1)),
+    ((9, 22, 120), (3, 4, 2)),
+    ((10, 17, 252), (4, 6, 3)),
+    ((5, 30, 236), (2, 8, 4)),
+    ((3, 12, 48), (1, 2, 4)),
+    ((5, 30, 232), (2, 8, 4)),
+    ((6, 20, 336), (3, 6, 6)),
+    ((4, 17, 464), (2, 8, 8)),
+]
+
+
+@pytest.mark.parametrize("shape,spacing", TENSOR_STORE, ids=[f"{s}-{d}" for s, d in TENSOR_STORE])
+def test_forward_tensor_store_blocks_match_oracle(shape, spacing):
+    phi = synth.uniform_phi(shape, spacing, -2, 2, seed=7 + sum(shape) + sum(spacing))
+    got = gpu_forward(phi, shape, spacing)
+    err, tol = fwd_err(got, phi, shape, spacing)
+    assert err <= tol, (err, tol)
+    b16 = gpu_forward(phi, shape, spacing, dtype=torch.bfloat16)
+    assert torch.equal(b16.cpu(), got.cpu().to(torch.bfloat16))
+
+
 @pytest.mark.parametrize("shape,spacing", SMALL[:10], ids=[f"{s}-{d}" for s, d in SMALL[:10]])
 def test_forward_bf16_is_rne_of_f32(shape, spacing):
     phi = synth.uniform_phi(shape, spacing, -4, 4, seed=3 + sum(shape))
