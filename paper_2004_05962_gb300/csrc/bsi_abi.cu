@@ -415,6 +415,19 @@ static cudaError_t run_group(const Group& g, Op op, bool bf16, float* part, long
         Batch<1> b;
         to_batch(g, b);
         if (op == Op::Forward) {
+            // BF16 at odd x-spacings >= 5: rows leave by tensor stores when strips of
+            // 24 tiles (g dx a multiple of 8: rows on 16-byte boundaries) take the place
+            // of the default 29, whose rows end off 16-byte boundaries (512 x 512 x 300
+            // at spacing 5: 0.153 -> 0.146 ms; at spacing 3 the idle lanes cost more:
+            // 512^3 0.414 -> 0.429 ms, not taken)
+            InstDesc& d0 = b.inst[0];
+            if (bf16 && !g.generic && (d0.dx & 1) && d0.dx >= 5 && d0.gcells == kGroupCells && d0.units > 0 &&
+                fwd_tma_rows(d0.X, d0.dx, d0.dy, kBf16OddStripTiles, true) > 0) {
+                d0.gcells = kBf16OddStripTiles;
+                d0.nxg = (int)cdiv(d0.ncx, d0.gcells);
+                d0.units = (long long)d0.ncz * d0.ncy * d0.nxg;
+                b.total_units = d0.units;
+            }
             const int rb = forward_tma_rows(b.inst[0], bf16, g.generic);
             if (rb > 0) {
                 CUtensorMap map;

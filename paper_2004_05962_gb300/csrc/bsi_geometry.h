@@ -223,6 +223,7 @@ BSI_HD int adj_warp_smem(int buf_bytes) { return kLoadStages * (16 + buf_bytes);
 // warp's kStoreStages blocks (128-byte aligned, plus a 128-byte slot the halo
 // lanes stage into) fit 1/16 of an SM's shared memory (two 8-warp CTAs).
 constexpr int kFwdTmaWarpBudget = 14 * 1024;
+constexpr int kBf16OddStripTiles = 24;   // BF16 strips at odd x-spacings on that path: 6 g dx % 16 == 0
 BSI_HD int pad128(int b) { return (b + 127) & ~127; }
 BSI_HD int fwd_tma_row_bytes(int gcells, int dx, bool bf16) { return gcells * dx * 3 * (bf16 ? 2 : 4); }
 BSI_HD int fwd_tma_warp_smem(int blk_bytes) { return kStoreStages * blk_bytes + 128; }

@@ -52,9 +52,9 @@ def test_forward_config_64cubed_seed1():
 
 
 # Volumes whose rows leave by tensor stores in blocks of rows (16-byte rows and
-# strips; FP32 at x-spacings <= 4, BF16 at even x-spacings with X % 8 == 0): one
-# to eight rows per block, ragged tails in x (a short last strip), y (a last
-# tile-row inside the volume shorter than the block) and z.
+# strips; FP32 at x-spacings <= 4, BF16 with X % 8 == 0 -- at odd x-spacings in
+# strips of 24 tiles): two to eight rows per block, ragged tails in x (a short
+# last strip), y (a last tile-row inside the volume shorter than the block) and z.
 TENSOR_STORE = [
     ((7, 13, 64), (2, 3, 1)),
     ((9, 22, 120), (3, 4, 2)),
@@ -64,6 +64,8 @@ TENSOR_STORE = [
     ((5, 30, 232), (2, 8, 4)),
     ((6, 20, 336), (3, 6, 6)),
     ((4, 17, 464), (2, 8, 8)),
+    ((6, 23, 248), (2, 5, 5)),
+    ((5, 14, 96), (3, 3, 3)),
 ]
 
 
