@@ -141,6 +141,8 @@ static void fill_desc(InstDesc& d, const bsi_geom& g, bool adjoint, bool bf16 = 
         d.ncy = (int)cdiv(g.Y, g.dy);
         d.ncz = (int)cdiv(g.Z, g.dz);
     }
+    d.jrows = 1;
+    d.ncyu = d.ncy;
     if (!adjoint) {
         d.gcells = cfg.fwd_strip_tiles > 0 ? cfg.fwd_strip_tiles : fwd_strip_tiles(d.X, d.dx, bf16);
         d.nxg = empty ? 0 : (int)cdiv(d.ncx, d.gcells);
@@ -150,14 +152,34 @@ static void fill_desc(InstDesc& d, const bsi_geom& g, bool adjoint, bool bf16 = 
         d.tma_rows = tma_block_rows(d.dx, d.dy);
         d.nxg = empty ? 0 : (int)cdiv(d.nx, kGroupCells);
         d.nzc = empty ? 0 : (int)cdiv(d.ncz, zchunk);
-        d.units = (long long)d.nzc * d.ncy * d.nxg;
+        d.units = (long long)d.nzc * d.ncyu * d.nxg;
     }
 }
 
 static void set_zchunk(InstDesc& d, int zc) {
     d.zchunk = zc;
     d.nzc = d.ncz > 0 ? (int)cdiv(d.ncz, zc) : 0;
-    d.units = (long long)d.nzc * d.ncy * d.nxg;
+    d.units = (long long)d.nzc * d.ncyu * d.nxg;
+}
+
+// Tile-rows per adjoint unit on the tensor-copy path where taken (the row path
+// takes 1): two tile-rows cut the partial sums' overlap in y from 4 units to
+// 2.5, so fewer are written and reduced.  Taken for single-volume calls at
+// y-spacings 4..6, where it measured faster (512 x 512 x 300 at spacing 5: the
+// forward + adjoint step 0.3192 -> 0.3140 ms; 512^3 at 4: 0.346 -> 0.326 ms,
+// at (6,5,4): 0.302 -> 0.274 ms), and not at y-spacing 3 (+1.5%: the 11-warp
+// register budget of two-row units) or 8 (+8.6%), nor in batches (a launch
+// more; +6% for the 64-volume batch).
+constexpr int kTmaJrows = 2;
+constexpr int kTmaJrowsMinDy = 4, kTmaJrowsMaxDy = 6;
+static bool two_row_units(const InstDesc& d, int n) {
+    return kTmaJrows > 1 && n == 1 && d.dy >= kTmaJrowsMinDy && d.dy <= kTmaJrowsMaxDy;
+}
+
+static void set_jrows(InstDesc& d, int jr) {
+    d.jrows = jr;
+    d.ncyu = d.ncy > 0 ? (int)cdiv(d.ncy, jr) : 0;
+    d.units = (long long)d.nzc * d.ncyu * d.nxg;
 }
 
 static long long adj_floats(const InstDesc& d) {
@@ -165,18 +187,25 @@ static long long adj_floats(const InstDesc& d) {
     return (f + 3) & ~3LL;  // keep every instance's partials 16-byte aligned
 }
 
-// Workspace floats an adjoint instance may need: for the table's zchunk if it
-// fixes one, else the most (least, with `least`) over every zchunk
-// choose_zchunk may pick.
+// Workspace floats an adjoint instance may need: the most (least, with
+// `least`) over every plan the launch may pick -- tile-rows per unit 1, or also
+// kTmaJrows where the volume could take the tensor-copy path, times the table's
+// zchunk if it fixes one, else every zchunk choose_zchunk may pick.
 static long long adj_floats_bound(const bsi_geom& g, bool least = false) {
     InstDesc d;
     fill_desc(d, g, true);
-    if (lookup_config(g.dx, g.dy, g.dz).adj_zchunk > 0) return adj_floats(d);
+    const bool fixed = lookup_config(g.dx, g.dy, g.dz).adj_zchunk > 0;
+    const int jrs[2] = {1, kTmaJrows};
+    const int njr = (two_row_units(d, 1) && d.units > 0 && d.dx <= kMaxSpecializedDx && d.X % 4 == 0) ? 2 : 1;
     long long m = -1;
-    for (int zc = kMinZChunk; zc <= kMaxZChunk; ++zc) {
-        set_zchunk(d, zc);
-        const long long f = adj_floats(d);
-        if (m < 0 || (least ? f < m : f > m)) m = f;
+    for (int k = 0; k < njr; ++k) {
+        set_jrows(d, jrs[k]);
+        for (int zc = kMinZChunk; zc <= kMaxZChunk; ++zc) {
+            if (!fixed) set_zchunk(d, zc);
+            const long long f = adj_floats(d);
+            if (m < 0 || (least ? f < m : f > m)) m = f;
+            if (fixed) break;
+        }
     }
     return m;
 }
@@ -219,7 +248,7 @@ static int choose_zchunk(const InstDesc& d0, bool tma, long long max_floats = -1
     int wps = 3 * kAdjWarpsMax;   // row path: three 4-warp CTAs per SM
     if (tma) {
         const int blk = tma_block_bytes(d0.dx, d0.tma_rows);
-        wps = tma_warps_per_cta(blk, tma_default_stages(blk), 0);
+        wps = tma_warps_per_cta(blk, tma_default_stages(blk), 0, d0.jrows);
     }
     const double slots = (double)device_sms() * wps;
     const double grad_bytes = 12.0 * d0.X * d0.Y * d0.Z;
@@ -238,7 +267,7 @@ static int choose_zchunk(const InstDesc& d0, bool tma, long long max_floats = -1
         const double full = (double)(long long)n, f = n - full;
         const double rounds = full + (f > 1e-9 ? 0.6 + 0.4 * f : 0.0);
         const double part_bytes = 4.0 * (double)adj_floats(d);
-        const double t = rounds / n * (grad_bytes + part_bytes) * (1.0 + 0.3 / zc) + part_bytes;
+        const double t = rounds / n * (grad_bytes + part_bytes) * (1.0 + 0.3 / (zc * d.jrows)) + part_bytes;
         if (best < 0 || t < best_t) {
             best = zc;
             best_t = t;
@@ -273,15 +302,18 @@ static bool tma_geometry_ok(const InstDesc& d) {
 static std::vector<Group> plan(const std::vector<InstDesc>& all, long long* ws_floats, bool allow_tma = false) {
     std::vector<Group> out;
     long long off = 0;
-    for (int pass = 0; pass < 3; ++pass) {
-        const bool tma = pass == 0, generic = pass == 2;
-        if (tma && !allow_tma) continue;
+    // passes: tensor-copy instances with 1, then kTmaJrows tile-rows per unit (one
+    // kernel instantiation each), the row path, the generic kernel
+    for (int pass = 0; pass < 4; ++pass) {
+        const bool tma = pass < 2, generic = pass == 3;
+        const int jr = pass == 1 ? kTmaJrows : 1;
+        if ((tma && !allow_tma) || (pass == 1 && kTmaJrows == 1)) continue;
         Group cur;
         cur.generic = generic;
         cur.tma = tma;
         for (const InstDesc& d0 : all) {
             const bool t = allow_tma && tma_geometry_ok(d0);
-            if (t != tma || (!t && (d0.dx > kMaxSpecializedDx) != generic)) continue;
+            if (t != tma || (t && d0.jrows != jr) || (!t && (d0.dx > kMaxSpecializedDx) != generic)) continue;
             InstDesc d = d0;
             d.part_off = off;
             off += adj_floats(d);
@@ -306,7 +338,7 @@ static std::vector<Group> plan(const std::vector<InstDesc>& all, long long* ws_f
     // order never changes any result.
     auto unit_cost = [](const InstDesc& d) {
         const long long planes = d.zchunk > 0 ? (long long)d.zchunk * d.dz : d.dz;
-        return planes * d.dy * (d.dx + 4);
+        return planes * d.jrows * d.dy * (d.dx + 4);
     };
     for (Group& g : out)
         std::stable_sort(g.inst.begin(), g.inst.end(),
@@ -491,8 +523,17 @@ static std::vector<InstDesc> descs(const bsi_instance* inst, int n, bool adjoint
         d.grad = inst[i].grad_field;
         d.dphi = inst[i].grad_phi;
         const bsi_geom& g = inst[i].geom;
-        if (adjoint && lookup_config(g.dx, g.dy, g.dz).adj_zchunk == 0)
-            set_zchunk(d, choose_zchunk(d, allow_tma && tma_geometry_ok(d), max_floats));
+        if (adjoint) {
+            const bool t = allow_tma && tma_geometry_ok(d);
+            const bool fixed = lookup_config(g.dx, g.dy, g.dz).adj_zchunk > 0;
+            if (t && two_row_units(d, n)) set_jrows(d, kTmaJrows);
+            if (!fixed) set_zchunk(d, choose_zchunk(d, t, max_floats));
+            if (d.jrows > 1 && max_floats >= 0 && adj_floats(d) > max_floats) {
+                // no plan of two tile-rows per unit fits the fixed scratch: one tile-row
+                set_jrows(d, 1);
+                if (!fixed) set_zchunk(d, choose_zchunk(d, t, max_floats));
+            }
+        }
     }
     return v;
 }
@@ -662,7 +703,7 @@ static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecke
                     if (abs0 != 3LL * d.dx * (u.col0 - kHalo + lane)) rc.fail("lane box offset", lane, abs0);
                 }
                 const int st = tma_default_stages(tsb);
-                const int w = tma_warps_per_cta(tsb, st, 0);
+                const int w = tma_warps_per_cta(tsb, st, 0, d.jrows);
                 if (st < kTmaMinStages || st > kTmaMaxStages || (long long)w * tma_warp_smem(tsb, st) + 128 > kTmaSmemBudget)
                     rc.fail("tensor-copy shared memory over budget", w, tsb);
             }
@@ -696,7 +737,7 @@ static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecke
                 const int j = lane - kHalo;
                 if (j < 0 || u.col0 + j >= d.nx) continue;
                 for (int pz = 0; pz < u.kz1 - u.kz0 + kHalo; ++pz)
-                    for (int m = 0; m < 4; ++m) {
+                    for (int m = 0; m < d.jrows + kHalo; ++m) {
                         const long long e = part_elem(d, ul, pz, m, j);
                         if (e < 0 || e + 3 > ws_floats) rc.fail("partial write", e, ws_floats);
                         else if (cover) written[(size_t)(e / 3)] = 1;
@@ -704,7 +745,7 @@ static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecke
             }
             for (int kz = u.kz0; kz < u.kz1; ++kz) {
                 const int z0 = kz * d.dz, zn = imin(d.dz, d.Z - z0);
-                const int y0 = u.jy * d.dy, yn = imin(d.dy, d.Y - y0);
+                const int y0 = u.jy * d.dy, yn = imin(d.jrows * d.dy, d.Y - y0);
                 for (int rz = 0; rz < zn; ++rz)
                     for (int ry = 0; ry < yn; ++ry) {
                         const long long e0 = field_elem(d, z0 + rz, y0 + ry, u.xs);
@@ -727,10 +768,12 @@ static void check_adjoint_group(const Group& g, long long ws_floats, RangeChecke
                         const int pz = gz - zc * d.zchunk;
                         const int planes = imin(d.zchunk, d.ncz - zc * d.zchunk) + kHalo;
                         if (pz >= planes) continue;
-                        for (int m = 0; m < 4; ++m) {
-                            const int jy = gy - m;
-                            if (jy < 0 || jy >= d.ncy) continue;
-                            const long long ul = ((long long)zc * d.ncy + jy) * d.nxg + xg;
+                        // the units whose tile-rows reach grid row gy, as the reduce finds them
+                        const int uy0 = gy / d.jrows, m0 = gy - uy0 * d.jrows;
+                        for (int q = 0; q < 4; ++q) {
+                            const int uy = uy0 - q, m = m0 + q * d.jrows;
+                            if (uy < 0 || uy >= d.ncyu || m >= d.jrows + kHalo) continue;
+                            const long long ul = ((long long)zc * d.ncyu + uy) * d.nxg + xg;
                             const long long e = part_elem(d, ul, pz, m, j);
                             if (e < 0 || e + 3 > ws_floats) rc.fail("partial read", e, ws_floats);
                             else if (cover && !written[(size_t)(e / 3)]) rc.fail("partial read before write", e, gx);

@@ -1,8 +1,9 @@
 // bsi_adjoint.cu -- adjoint (transpose of Eq. 1) kernels and their launchers.
 //
-// Phase 1 (bsi_adjoint_partials_kernel): each warp unit walks a chunk of
-// tile-planes of one tile-row and one x-group and writes the complete-in-x,
-// partial-in-y/z sums of its (chunk+3) x 4 x 29 control points.
+// Phase 1 (bsi_adjoint_partials_kernel, bsi_adjoint_partials_tma_kernel): each
+// warp unit walks a chunk of tile-planes of one tile-row (two on the
+// tensor-copy path where chosen) and one x-group and writes the complete-in-x,
+// partial-in-y/z sums of its (chunk+3) x (tile-rows+3) x 29 control points.
 // Phase 2 (bsi_adjoint_reduce_kernel): each control point sums the <= 2 x 4
 // partials that cover it, in a fixed order, and writes grad_phi.
 #include "bsi_kernels.cuh"
@@ -69,8 +70,8 @@ __global__ void __launch_bounds__(kAdjMaxWarps * kLanes, 3)
 // One CTA per SM with as many warps as the stage rings fit in shared memory;
 // warp w's ring of b.stages stages of b.buf_bytes sits after its 128 bytes of
 // mbarriers.
-template <int MAXB>
-__global__ void __launch_bounds__(kTmaMaxWarps * kLanes, 1)
+template <int MAXB, int JR>
+__global__ void __launch_bounds__((JR == 1 ? kTmaMaxWarps : kTmaMaxWarps2) * kLanes, 1)
     bsi_adjoint_partials_tma_kernel(const __grid_constant__ Batch<MAXB> b, const __grid_constant__ TmaMaps<MAXB> maps,
                                     float* __restrict__ part, long long ws_floats) {
     extern __shared__ __align__(128) unsigned char tsmem[];
@@ -102,14 +103,14 @@ __global__ void __launch_bounds__(kTmaMaxWarps * kLanes, 1)
         const long long ul = uu - d.unit_begin;
         bool ok;
         switch (d.dx) {
-            case 1: ok = adjoint_unit_tma<1>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
-            case 2: ok = adjoint_unit_tma<2>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
-            case 3: ok = adjoint_unit_tma<3>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
-            case 4: ok = adjoint_unit_tma<4>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
-            case 5: ok = adjoint_unit_tma<5>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
-            case 6: ok = adjoint_unit_tma<6>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
-            case 7: ok = adjoint_unit_tma<7>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
-            default: ok = adjoint_unit_tma<8>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            case 1: ok = adjoint_unit_tma<1, JR>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            case 2: ok = adjoint_unit_tma<2, JR>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            case 3: ok = adjoint_unit_tma<3, JR>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            case 4: ok = adjoint_unit_tma<4, JR>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            case 5: ok = adjoint_unit_tma<5, JR>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            case 6: ok = adjoint_unit_tma<6, JR>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            case 7: ok = adjoint_unit_tma<7, JR>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
+            default: ok = adjoint_unit_tma<8, JR>(d, tm, ul, bars, ring, b.buf_bytes, b.stages, lane, q, part, ws_floats, &g_err); break;
         }
         if (!ok) break;  // a lost box: the error word says so; stop this warp
     }
@@ -123,8 +124,9 @@ __global__ void __launch_bounds__(kTmaMaxWarps * kLanes, 1)
 
 // One thread per stored control point of every instance.  The units that
 // cover point (gx, gy, gz): x-group gx / 29 (columns are complete within a
-// unit), tile-rows jy = gy - m for m = 0..3, and the tile-plane chunks whose
-// plane window [chunk start, chunk start + planes + 3) contains gz.
+// unit), the units whose tile-rows [jy, jy + jrows) reach grid row gy (tile-rows
+// gy - 3 .. gy), and the tile-plane chunks whose plane window [chunk start,
+// chunk start + planes + 3) contains gz.
 template <int MAXB>
 __global__ void __launch_bounds__(256)
     bsi_adjoint_reduce_kernel(const __grid_constant__ Batch<MAXB> b, const float* __restrict__ part,
@@ -158,34 +160,37 @@ __global__ void __launch_bounds__(256)
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
         if (d.nzc > 0) {
             // The covering partials: at most two tile-plane chunks (zc_hi - 1, zc_hi)
-            // times four tile-rows.  Their offsets differ by constants of the
-            // instance: e(t, m) = e(0, 0) + t sz - m sy (part_elem written out),
-            // so one 64-bit offset per point and adds give all eight.  All 8 x 3
-            // loads are issued before any sum, and the sum runs in the fixed
-            // order (chunk, row); channels 0 and 1 are added as packed pairs
+            // times four unit rows, uy0 - q (q = 0..3), each holding grid row gy as its
+            // row m0 + q jrows when that is below jrows + 3.  Their offsets differ by
+            // constants of the instance: e(t, q) = e(0, 0) + t sz - q sy (part_elem
+            // written out), so one 64-bit offset per point and adds give all eight.
+            // All 8 x 3 loads are issued before any sum, and the sum runs in the
+            // fixed order (chunk, row); channels 0 and 1 are added as packed pairs
             // (bitwise the scalar sums).
             const int zc_hi = imin(d.nzc - 1, gz / d.zchunk);
+            const int jr = d.jrows, nr = jr + kHalo;
+            const int uy0 = jr == 2 ? gy >> 1 : gy, m0 = gy - uy0 * jr;
             const long long uf = adj_unit_floats(d);
-            const long long sy = (long long)d.nxg * uf - (long long)kGroupCells * 3;       // one tile-row less
-            const long long sz = (long long)d.ncy * d.nxg * uf - (long long)d.zchunk * 4 * kGroupCells * 3;  // next chunk
+            const long long sy = (long long)d.nxg * uf - (long long)jr * kGroupCells * 3;   // one unit row less
+            const long long sz = (long long)d.ncyu * d.nxg * uf - (long long)d.zchunk * nr * kGroupCells * 3;  // next chunk
             const int zc0 = zc_hi - 1, pz0 = gz - zc0 * d.zchunk;
-            const long long e00 = d.part_off + (((long long)zc0 * d.ncy + gy) * d.nxg + xg) * uf +
-                                  ((long long)pz0 * 4 * kGroupCells + j) * 3;
+            const long long e00 = d.part_off + (((long long)zc0 * d.ncyu + uy0) * d.nxg + xg) * uf +
+                                  (((long long)pz0 * nr + m0) * kGroupCells + j) * 3;
             float v[2][4][3];
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
                 const int zc = zc0 + t;
                 const bool zok = zc >= 0 && pz0 - t * d.zchunk < imin(d.zchunk, d.ncz - zc * d.zchunk) + kHalo;
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    const int jy = gy - m;
-                    v[t][m][0] = v[t][m][1] = v[t][m][2] = 0.f;
-                    if (zok && jy >= 0 && jy < d.ncy) {
-                        const long long e = e00 + t * sz - m * sy;
+                for (int q = 0; q < 4; ++q) {
+                    const int uy = uy0 - q;
+                    v[t][q][0] = v[t][q][1] = v[t][q][2] = 0.f;
+                    if (zok && uy >= 0 && uy < d.ncyu && m0 + q * jr < nr) {
+                        const long long e = e00 + t * sz - q * sy;
                         BSI_GUARD(e >= 0 && e + 3 <= ws_floats, kErrPartRead, &g_err) {
-                            v[t][m][0] = __ldcs(part + e);
-                            v[t][m][1] = __ldcs(part + e + 1);
-                            v[t][m][2] = __ldcs(part + e + 2);
+                            v[t][q][0] = __ldcs(part + e);
+                            v[t][q][1] = __ldcs(part + e + 1);
+                            v[t][q][2] = __ldcs(part + e + 2);
                         }
                     }
                 }
@@ -238,10 +243,12 @@ cudaError_t launch_adjoint_partials(const Batch<MAXB>& b, bool generic, float* p
 }
 
 // Warps per CTA of the tensor-copy kernel: as many as the rings fit in one
-// SM's shared memory (<= kTmaMaxWarps), at most `req` when that is set.
-int tma_warps_per_cta(int stage_bytes, int stages, int req) {
+// SM's shared memory (<= kTmaMaxWarps, or kTmaMaxWarps2 for units of two
+// tile-rows), at most `req` when that is set.
+int tma_warps_per_cta(int stage_bytes, int stages, int req, int jrows) {
+    const int wmax = jrows > 1 ? kTmaMaxWarps2 : kTmaMaxWarps;
     int w = (kTmaSmemBudget - 128) / tma_warp_smem(stage_bytes, stages);
-    if (w > kTmaMaxWarps) w = kTmaMaxWarps;
+    if (w > wmax) w = wmax;
     if (req > 0 && req < w) w = req;
     return w < 1 ? 1 : w;
 }
@@ -249,8 +256,10 @@ int tma_warps_per_cta(int stage_bytes, int stages, int req) {
 template <int MAXB>
 cudaError_t launch_adjoint_partials_tma(const Batch<MAXB>& b, const TmaMaps<MAXB>& maps, float* part,
                                         long long ws_floats, cudaStream_t s, LaunchInfo* info) {
-    auto kern = bsi_adjoint_partials_tma_kernel<MAXB>;
-    const int wpc = tma_warps_per_cta(b.buf_bytes, b.stages, b.warps_req);
+    // every instance of a tensor-copy launch has the same tile-rows per unit
+    const int jr = b.inst[0].jrows > 1 ? 2 : 1;
+    auto kern = jr == 2 ? bsi_adjoint_partials_tma_kernel<MAXB, 2> : bsi_adjoint_partials_tma_kernel<MAXB, 1>;
+    const int wpc = tma_warps_per_cta(b.buf_bytes, b.stages, b.warps_req, jr);
     const int threads = wpc * kLanes;
     const int smem = wpc * tma_warp_smem(b.buf_bytes, b.stages) + 128;
     KernelFacts f;

@@ -44,6 +44,8 @@ struct InstDesc {
     int gcells;          // forward: tiles per warp strip (<= 29; see fwd_strip_tiles)
     int warps_req;       // requested warps per CTA from the tile-config table (0: automatic)
     int tma_rows;        // adjoint tensor-copy path: rows per block (tma_block_rows), else 0
+    int jrows;           // adjoint: tile-rows per unit (1, or 2 on the tensor-copy path)
+    int ncyu;            // adjoint: unit rows, ceil(ncy / jrows)
     long long units;        // units of this instance
     long long unit_begin;   // first global unit index of this instance in its launch
     long long point_begin;  // adjoint reduce: first global grid point of this instance
@@ -164,7 +166,7 @@ BSI_HD FwdUnit fwd_unit(const InstDesc& d, long long ul) {
 // ---------------------------------------------------------------- adjoint
 
 struct AdjUnit {
-    int zc, jy, xg;
+    int zc, jy, xg;   // jy: the unit's first tile-row (it takes jrows of them)
     int col0;    // first complete column; lane l holds tile / column col0 - 3 + l
     int xs;      // first voxel read by the warp
     int nvox;    // voxels per row read by the warp
@@ -175,8 +177,8 @@ BSI_HD AdjUnit adj_unit(const InstDesc& d, long long ul) {
     AdjUnit u;
     u.xg = (int)(ul % d.nxg);
     const long long t = ul / d.nxg;
-    u.jy = (int)(t % d.ncy);
-    u.zc = (int)(t / d.ncy);
+    u.jy = (int)(t % d.ncyu) * d.jrows;
+    u.zc = (int)(t / d.ncyu);
     u.col0 = u.xg * kGroupCells;
     const int c_lo = imax(0, u.col0 - kHalo);
     const int c_hi = imin(d.ncx, u.col0 + kGroupCells);
@@ -187,14 +189,16 @@ BSI_HD AdjUnit adj_unit(const InstDesc& d, long long ul) {
     return u;
 }
 
-// Floats of partial sums one adjoint unit writes: (zchunk + 3) planes x 4 rows
-// x 29 columns x 3 channels.
+// Floats of partial sums one adjoint unit writes: (zchunk + 3) planes x
+// (jrows + 3) grid rows x 29 columns x 3 channels.
 BSI_HD long long adj_unit_floats(const InstDesc& d) {
-    return (long long)(d.zchunk + kHalo) * 4 * kGroupCells * 3;
+    return (long long)(d.zchunk + kHalo) * (d.jrows + kHalo) * kGroupCells * 3;
 }
 
+// Partial sum of a unit: grid plane pz of its window, grid row m (0 .. jrows + 2,
+// from its first tile-row), column j.
 BSI_HD long long part_elem(const InstDesc& d, long long ul, int pz, int m, int j) {
-    return d.part_off + ul * adj_unit_floats(d) + (((long long)pz * 4 + m) * kGroupCells + j) * 3;
+    return d.part_off + ul * adj_unit_floats(d) + (((long long)pz * (d.jrows + kHalo) + m) * kGroupCells + j) * 3;
 }
 
 // Staging buffer bytes for a largest x-spacing dxmax: one row segment of up to
@@ -268,6 +272,7 @@ constexpr int kTmaBlockTarget = 14 * 1024;       // largest block that still lea
 constexpr int kTmaMinStages = 2;
 constexpr int kTmaMaxStages = 4;
 constexpr int kTmaMaxWarps = 12;                 // register budget: 12 warps x 32 x 170 <= 65536
+constexpr int kTmaMaxWarps2 = 11;                // two tile-rows per unit: 11 warps x 32 x 186
 constexpr int kTmaSmemBudget = 227 * 1024;       // one CTA per SM takes all of its shared memory
 
 // Rows per block for spacing (dx, dy): the largest divisor of dy up to

@@ -472,15 +472,16 @@ __device__ __forceinline__ void forward_unit_tma(const InstDesc& d, const void* 
 
 // ------------------------------------------------------------------ adjoint
 
-// Writes one completed grid plane of a unit's partial sums (lanes 3..31 hold
-// the 29 complete columns).
+// Writes one completed grid plane of a unit's partial sums, NR = jrows + 3 grid
+// rows (lanes 3..31 hold the 29 complete columns).
+template <int NR>
 __device__ __forceinline__ void flush_plane(const InstDesc& d, long long ul, int pz, const AdjUnit& u,
-                                            int lane, const float (&h)[4][3], float* part,
+                                            int lane, const float (&h)[NR][3], float* part,
                                             long long ws_floats, unsigned* err) {
     const int j = lane - kHalo;
     if (j >= 0 && u.col0 + j < d.nx) {
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
+        for (int m = 0; m < NR; ++m) {
             const long long e = part_elem(d, ul, pz, m, j);
             BSI_GUARD(e >= 0 && e + 3 <= ws_floats, kErrPartWrite, err) {
                 part[e] = h[m][0];
@@ -566,9 +567,12 @@ __device__ __forceinline__ void gather_tile(float (&q4)[4][3], uint32_t sv) {
 
 // Column sum and y-stage of one row: the column of lane l collects q4[k] of the
 // tile k lanes below, h = ((q4[0] + q4[1]') + q4[2]'') + q4[3]''' per channel,
-// and hy[m] += b_m h; channels 0 and 1 packed (bitwise the scalar form).
-__device__ __forceinline__ void column_sum_y(const float (&q4)[4][3], float (&hy)[4][3], float b0, float b1,
+// and hy[OFF + m] += b_m h (OFF: the row's tile-row within the unit); channels
+// 0 and 1 packed (bitwise the scalar form).
+template <int OFF = 0, int NR = 4>
+__device__ __forceinline__ void column_sum_y(const float (&q4)[4][3], float (&hy)[NR][3], float b0, float b1,
                                              float b2, float b3) {
+    static_assert(OFF + 4 <= NR, "four grid rows from OFF");
     float s1[3], s2[3], s3[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -580,17 +584,18 @@ __device__ __forceinline__ void column_sum_y(const float (&q4)[4][3], float (&hy
     h = __fadd2_rn(h, make_float2(s2[0], s2[1]));
     h = __fadd2_rn(h, make_float2(s3[0], s3[1]));
     const float h2 = q4[0][2] + s1[2] + s2[2] + s3[2];
-    fma3(hy[0], b0, h.x, h.y, h2);
-    fma3(hy[1], b1, h.x, h.y, h2);
-    fma3(hy[2], b2, h.x, h.y, h2);
-    fma3(hy[3], b3, h.x, h.y, h2);
+    fma3(hy[OFF], b0, h.x, h.y, h2);
+    fma3(hy[OFF + 1], b1, h.x, h.y, h2);
+    fma3(hy[OFF + 2], b2, h.x, h.y, h2);
+    fma3(hy[OFF + 3], b3, h.x, h.y, h2);
 }
 
-// z-stage of one voxel plane: hz[n][m] += a_n hy[m].
-__device__ __forceinline__ void accumulate_z(float (&hz)[4][4][3], const float (&hy)[4][3], float a0, float a1,
+// z-stage of one voxel plane: hz[n][m] += a_n hy[m] over the unit's NR grid rows.
+template <int NR>
+__device__ __forceinline__ void accumulate_z(float (&hz)[4][NR][3], const float (&hy)[NR][3], float a0, float a1,
                                              float a2, float a3) {
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
+    for (int m = 0; m < NR; ++m) {
         fma3(hz[0][m], a0, hy[m][0], hy[m][1], hy[m][2]);
         fma3(hz[1][m], a1, hy[m][0], hy[m][1], hy[m][2]);
         fma3(hz[2][m], a2, hy[m][0], hy[m][1], hy[m][2]);
@@ -769,7 +774,9 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
     return true;
 }
 
-// One adjoint unit on the tensor-copy path (see tma_boxes): block k of the
+// One adjoint unit on the tensor-copy path (see tma_boxes), JR tile-rows (1 or
+// 2; with 2 a control point's partial sums overlap over 2.5 units in y instead
+// of 4, so fewer partial sums are written and reduced): block k of the
 // unit (rows [i rb, i rb + rb) of voxel plane p, k = p * nblk + i) arrives as
 // one or two boxes in ring stage (q0 + k) % stages, issued `stages` blocks
 // ahead by lane 0; a warp waits once per block.  Halo, cut and empty tiles read
@@ -781,7 +788,7 @@ __device__ __forceinline__ bool adjoint_unit(const InstDesc& d, long long ul, ui
 // three interleaved runs), where the adjoint is bound by its reads.
 constexpr bool kTmaGatherPacked = false;
 
-template <int DX>
+template <int DX, int JR>
 __device__ __forceinline__ bool adjoint_unit_tma(const InstDesc& d, const void* tmap, long long ul,
                                                  uint64_t* bars, unsigned char* ring, int stage_bytes, int stages,
                                                  int lane, unsigned& q, float* part, long long ws_floats,
@@ -795,8 +802,9 @@ __device__ __forceinline__ bool adjoint_unit_tma(const InstDesc& d, const void* 
     const int f0 = tma_first_float(u, DX);
     const int gx0 = tma_group_of(f0);
     const int shift = f0 - 4 * gx0;                         // 0..3 floats
-    const int y0 = u.jy * d.dy, yn = imin(d.dy, d.Y - y0);
-    const int nblk = (yn + rb - 1) / rb;                    // blocks per voxel plane of this tile-row
+    constexpr int NR = JR + kHalo;                          // grid rows the unit's sums reach
+    const int y0 = u.jy * d.dy, yn = imin(JR * d.dy, d.Y - y0);
+    const int nblk = (yn + rb - 1) / rb;                    // blocks per voxel plane of the unit's tile-rows
     const int zb = u.kz0 * d.dz;
     const int planes = imin(u.kz1 * d.dz, d.Z) - zb;
     const int blocks = planes * nblk;
@@ -826,11 +834,11 @@ __device__ __forceinline__ bool adjoint_unit_tma(const InstDesc& d, const void* 
     const int bl = NB == 1 ? 0 : lane >> 4;                // this lane's box
     const uint32_t lane_off = (uint32_t)(bl * box_pad) + 4u * (uint32_t)shift + 12u * DX * (uint32_t)(lane - 16 * bl);
 
-    float hz[4][4][3];
+    float hz[4][NR][3];
 #pragma unroll
     for (int n = 0; n < 4; ++n)
 #pragma unroll
-        for (int m = 0; m < 4; ++m)
+        for (int m = 0; m < NR; ++m)
 #pragma unroll
             for (int c = 0; c < 3; ++c) hz[n][m][c] = 0.f;
 
@@ -838,9 +846,9 @@ __device__ __forceinline__ bool adjoint_unit_tma(const InstDesc& d, const void* 
     for (int kz = u.kz0; kz < u.kz1; ++kz) {
         const int z0 = kz * d.dz, zn = imin(d.dz, d.Z - z0);
         for (int rz = 0; rz < zn; ++rz) {
-            float hy[4][3];
+            float hy[NR][3];
 #pragma unroll
-            for (int m = 0; m < 4; ++m)
+            for (int m = 0; m < NR; ++m)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) hy[m][c] = 0.f;
             for (int i = 0; i < nblk; ++i, ++k) {
@@ -869,9 +877,17 @@ __device__ __forceinline__ bool adjoint_unit_tma(const InstDesc& d, const void* 
                         for (int c = 0; c < 3; ++c) q4[l][c] = 0.f;
                     // 16-byte loads for DX = 4, 8: shift is then 0, box rows are 16-byte multiples
                     gather_tile<DX, DX % 4 == 0 ? 4 : 1, kTmaGatherPacked>(q4, sv + (uint32_t)(r * row_bytes));
-                    const float b0 = c_lut.w[wyb + 4 * ry], b1 = c_lut.w[wyb + 4 * ry + 1];
-                    const float b2 = c_lut.w[wyb + 4 * ry + 2], b3 = c_lut.w[wyb + 4 * ry + 3];
-                    column_sum_y(q4, hy, b0, b1, b2, b3);
+                    // the row's tile-row within the unit (0 or 1) and its offset in that tile-row
+                    const int t = (JR > 1 && ry >= d.dy) ? 1 : 0;
+                    const int rr = ry - t * d.dy;
+                    const float b0 = c_lut.w[wyb + 4 * rr], b1 = c_lut.w[wyb + 4 * rr + 1];
+                    const float b2 = c_lut.w[wyb + 4 * rr + 2], b3 = c_lut.w[wyb + 4 * rr + 3];
+                    if constexpr (JR > 1) {
+                        if (t) column_sum_y<1>(q4, hy, b0, b1, b2, b3);
+                        else column_sum_y<0>(q4, hy, b0, b1, b2, b3);
+                    } else {
+                        column_sum_y<0>(q4, hy, b0, b1, b2, b3);
+                    }
                 }
                 // the stage may be refilled once every lane has read it
                 fence_proxy_async_smem();
@@ -886,11 +902,11 @@ __device__ __forceinline__ bool adjoint_unit_tma(const InstDesc& d, const void* 
 #pragma unroll
         for (int n = 0; n < 3; ++n)
 #pragma unroll
-            for (int m = 0; m < 4; ++m)
+            for (int m = 0; m < NR; ++m)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) hz[n][m][c] = hz[n + 1][m][c];
 #pragma unroll
-        for (int m = 0; m < 4; ++m)
+        for (int m = 0; m < NR; ++m)
 #pragma unroll
             for (int c = 0; c < 3; ++c) hz[3][m][c] = 0.f;
     }

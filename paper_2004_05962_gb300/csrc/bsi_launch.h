@@ -77,7 +77,7 @@ struct TmaMaps {
     CUtensorMap m[MAXB];
 };
 
-int tma_warps_per_cta(int stage_bytes, int stages, int req);
+int tma_warps_per_cta(int stage_bytes, int stages, int req, int jrows = 1);
 
 template <int MAXB>
 cudaError_t launch_adjoint_partials_tma(const Batch<MAXB>& b, const TmaMaps<MAXB>& maps, float* part,

@@ -150,6 +150,11 @@ TMA = [
     ((9, 30, 40), (2, 10, 3)),      # dy = 10: blocks of 5 rows
     ((7, 25, 48), (3, 11, 4)),      # dy = 11 (prime): blocks of 1 row
     ((6, 35, 264), (2, 16, 8)),     # dx = 8, dy = 16: two boxes of 4 rows
+    # y-spacings 4..6: units of two tile-rows (single-volume calls), odd and even
+    # tile-row counts, several tile-plane chunks
+    ((8, 40, 64), (2, 6, 4)),
+    ((13, 24, 100), (5, 4, 3)),
+    ((40, 18, 48), (3, 5, 4)),
 ]
 
 
@@ -163,10 +168,14 @@ def test_adjoint_tensor_copy_path_matches_oracle(shape, spacing):
 
 
 @pytest.mark.parametrize("shape,spacing", TMA[1::2], ids=[f"{s}-{d}" for s, d in TMA[1::2]])
-def test_adjoint_tensor_copy_and_row_paths_agree_bitwise(shape, spacing):
-    """The same gradient 16-byte aligned (tensor-copy path) and 4 bytes off
-    (row path): both paths add the same terms in the same order."""
-    g = torch.from_numpy(synth.normal_field(shape, seed=7 + sum(shape))).to(dev())
+def test_adjoint_tensor_copy_and_row_paths_agree(shape, spacing):
+    """The same gradient 16-byte aligned (tensor-copy path) and 4 bytes off (row
+    path).  With one tile-row per unit both paths add the same terms in the same
+    order: bitwise equal.  A single volume at y-spacing 4..6 takes units of two
+    tile-rows on the tensor-copy path, which sum a control point's terms in
+    another order: there both results must match the oracle."""
+    g_np = synth.normal_field(shape, seed=7 + sum(shape))
+    g = torch.from_numpy(g_np).to(dev())
     n = g.numel()
     buf = torch.empty(n + 4, device=dev())
     assert buf.data_ptr() % 16 == 0
@@ -175,7 +184,12 @@ def test_adjoint_tensor_copy_and_row_paths_agree_bitwise(shape, spacing):
     a = P.bsi_field_adjoint(g.contiguous(), spacing)
     b = P.bsi_field_adjoint(off, spacing)
     torch.cuda.synchronize()
-    assert torch.equal(a, b)
+    if 4 <= spacing[1] <= 6:
+        for got in (a, b):
+            err, tol = adj_err(got, g_np, spacing)
+            assert err <= tol, (err, tol)
+    else:
+        assert torch.equal(a, b)
 
 
 def test_empty_volumes():
