@@ -127,7 +127,7 @@ __global__ void __launch_bounds__((JR == 1 ? kTmaMaxWarps : kTmaMaxWarps2) * kLa
 // unit), the units whose tile-rows [jy, jy + jrows) reach grid row gy (tile-rows
 // gy - 3 .. gy), and the tile-plane chunks whose plane window [chunk start,
 // chunk start + planes + 3) contains gz.
-template <int MAXB>
+template <int MAXB, int JR>
 __global__ void __launch_bounds__(256)
     bsi_adjoint_reduce_kernel(const __grid_constant__ Batch<MAXB> b, const float* __restrict__ part,
                               long long ws_floats) {
@@ -168,8 +168,8 @@ __global__ void __launch_bounds__(256)
             // fixed order (chunk, row); channels 0 and 1 are added as packed pairs
             // (bitwise the scalar sums).
             const int zc_hi = imin(d.nzc - 1, gz / d.zchunk);
-            const int jr = d.jrows, nr = jr + kHalo;
-            const int uy0 = jr == 2 ? gy >> 1 : gy, m0 = gy - uy0 * jr;
+            constexpr int jr = JR, nr = JR + kHalo;   // every instance of a launch has JR tile-rows per unit
+            const int uy0 = JR == 2 ? gy >> 1 : gy, m0 = gy - uy0 * JR;
             const long long uf = adj_unit_floats(d);
             const long long sy = (long long)d.nxg * uf - (long long)jr * kGroupCells * 3;   // one unit row less
             const long long sz = (long long)d.ncyu * d.nxg * uf - (long long)d.zchunk * nr * kGroupCells * 3;  // next chunk
@@ -276,7 +276,7 @@ cudaError_t launch_adjoint_partials_tma(const Batch<MAXB>& b, const TmaMaps<MAXB
 template <int MAXB>
 cudaError_t launch_adjoint_reduce(const Batch<MAXB>& b, const float* part, long long ws_floats, cudaStream_t s,
                                   LaunchInfo* info) {
-    auto kern = bsi_adjoint_reduce_kernel<MAXB>;
+    auto kern = b.inst[0].jrows > 1 ? bsi_adjoint_reduce_kernel<MAXB, 2> : bsi_adjoint_reduce_kernel<MAXB, 1>;
     KernelFacts f;
     cudaError_t e = kernel_facts(reinterpret_cast<const void*>(kern), 256, 0, &f);
     if (e != cudaSuccess) return e;
