@@ -83,9 +83,10 @@ cudaError_t launch_forward(const Batch<MAXB>& b, bool bf16, bool generic, cudaSt
     return generic ? launch_fwd_t<MAXB, false, true>(b, s, info) : launch_fwd_t<MAXB, false, false>(b, s, info);
 }
 
-// Forward on the tensor-store path (one volume; see fwd_tma_rows): the same
-// persistent unit walk as bsi_forward_kernel, rows leaving in blocks of rb.
-template <bool BF16>
+// Forward on the tensor-store path (one volume, C = 3 or 1 channels; see
+// fwd_tma_rows): the same persistent unit walk as bsi_forward_kernel, rows
+// leaving in blocks of rb.
+template <bool BF16, int C>
 __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
     bsi_forward_tma_kernel(const __grid_constant__ Batch<1> b, const __grid_constant__ CUtensorMap map, int rb,
                            int blk_bytes) {
@@ -103,14 +104,14 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
         const long long ul = slot_unit(r, blockIdx.x, warp, gridDim.x, wpc, b.total_units, false);
         if (ul < 0) break;
         switch (d.dx) {
-            case 1: forward_unit_tma<1, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
-            case 2: forward_unit_tma<2, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
-            case 3: forward_unit_tma<3, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
-            case 4: forward_unit_tma<4, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
-            case 5: forward_unit_tma<5, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
-            case 6: forward_unit_tma<6, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
-            case 7: forward_unit_tma<7, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
-            default: forward_unit_tma<8, BF16>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            case 1: forward_unit_tma<1, BF16, C>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            case 2: forward_unit_tma<2, BF16, C>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            case 3: forward_unit_tma<3, BF16, C>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            case 4: forward_unit_tma<4, BF16, C>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            case 5: forward_unit_tma<5, BF16, C>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            case 6: forward_unit_tma<6, BF16, C>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            case 7: forward_unit_tma<7, BF16, C>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
+            default: forward_unit_tma<8, BF16, C>(d, &map, ul, stage, blk_bytes, rb, lane, ring, &g_err); break;
         }
     }
     // the blocks must outlive every tensor store that reads them
@@ -119,16 +120,16 @@ __global__ void __launch_bounds__(kMaxWarpsPerCta * kLanes, 2)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-cudaError_t launch_forward_tma(const Batch<1>& b, bool bf16, const CUtensorMap& map, int rb, cudaStream_t s,
-                               LaunchInfo* info) {
+template <bool BF16, int C>
+static cudaError_t launch_fwd_tma_t(const Batch<1>& b, const CUtensorMap& map, int rb, cudaStream_t s,
+                                    LaunchInfo* info) {
     const InstDesc& d = b.inst[0];
-    const int blk_bytes = pad128(rb * fwd_tma_row_bytes(d.gcells, d.dx, bf16));
+    const int blk_bytes = pad128(rb * fwd_tma_row_bytes(d.gcells, d.dx, BF16, C));
     const int wsm = fwd_tma_warp_smem(blk_bytes);
     const int wpc = warps_per_cta(wsm, b.warps_req);
     const int threads = wpc * kLanes;
     const int smem = wpc * wsm + 128;
-    const void* kern = bf16 ? reinterpret_cast<const void*>(bsi_forward_tma_kernel<true>)
-                            : reinterpret_cast<const void*>(bsi_forward_tma_kernel<false>);
+    const void* kern = reinterpret_cast<const void*>(bsi_forward_tma_kernel<BF16, C>);
     KernelFacts f;
     cudaError_t e = kernel_facts(kern, threads, smem, &f);
     if (e != cudaSuccess) return e;
@@ -137,8 +138,14 @@ cudaError_t launch_forward_tma(const Batch<1>& b, bool bf16, const CUtensorMap& 
     const int grid = (int)(want < cap ? want : cap);
     if (info) *info = LaunchInfo{grid, threads, smem, f.ctas_per_sm};
     if (grid <= 0) return cudaSuccess;
-    if (bf16) return launch_pdl(bsi_forward_tma_kernel<true>, grid, threads, smem, s, b, map, rb, blk_bytes);
-    return launch_pdl(bsi_forward_tma_kernel<false>, grid, threads, smem, s, b, map, rb, blk_bytes);
+    return launch_pdl(bsi_forward_tma_kernel<BF16, C>, grid, threads, smem, s, b, map, rb, blk_bytes);
+}
+
+cudaError_t launch_forward_tma(const Batch<1>& b, bool bf16, int channels, const CUtensorMap& map, int rb,
+                               cudaStream_t s, LaunchInfo* info) {
+    if (channels == 1)
+        return bf16 ? launch_fwd_tma_t<true, 1>(b, map, rb, s, info) : launch_fwd_tma_t<false, 1>(b, map, rb, s, info);
+    return bf16 ? launch_fwd_tma_t<true, 3>(b, map, rb, s, info) : launch_fwd_tma_t<false, 3>(b, map, rb, s, info);
 }
 
 // Scalar (one-channel) interpolation of a single volume.

@@ -229,7 +229,7 @@ BSI_HD int adj_warp_smem(int buf_bytes) { return kLoadStages * (16 + buf_bytes);
 constexpr int kFwdTmaWarpBudget = 14 * 1024;
 constexpr int kBf16OddStripTiles = 24;   // BF16 strips at odd x-spacings on that path: 6 g dx % 16 == 0
 BSI_HD int pad128(int b) { return (b + 127) & ~127; }
-BSI_HD int fwd_tma_row_bytes(int gcells, int dx, bool bf16) { return gcells * dx * 3 * (bf16 ? 2 : 4); }
+BSI_HD int fwd_tma_row_bytes(int gcells, int dx, bool bf16, int c = 3) { return gcells * dx * c * (bf16 ? 2 : 4); }
 BSI_HD int fwd_tma_warp_smem(int blk_bytes) { return kStoreStages * blk_bytes + 128; }
 
 // Rows per block of the tensor-store path, or 0 where it does not apply
@@ -238,9 +238,9 @@ BSI_HD int fwd_tma_warp_smem(int blk_bytes) { return kStoreStages * blk_bytes + 
 // Measured on 512^3: FP32 at spacing 3 0.389 -> 0.352 ms and at 4 0.269 ->
 // 0.250 ms (bound by per-row work); BF16 at 4, 6, 8 14-16% faster; FP32 at 6,
 // already at the write roofline, 0.231 -> 0.246 ms (so not taken).
-BSI_HD int fwd_tma_rows(int X, int dx, int dy, int gcells, bool bf16) {
-    const int rowb = fwd_tma_row_bytes(gcells, dx, bf16);
-    if (dx < 1 || dx > (bf16 ? kMaxSpecializedDx : 4) || (3 * X * (bf16 ? 2 : 4)) % 16 != 0 || rowb % 16 != 0 ||
+BSI_HD int fwd_tma_rows(int X, int dx, int dy, int gcells, bool bf16, int c = 3) {
+    const int rowb = fwd_tma_row_bytes(gcells, dx, bf16, c);
+    if (dx < 1 || dx > (bf16 ? kMaxSpecializedDx : 4) || (c * X * (bf16 ? 2 : 4)) % 16 != 0 || rowb % 16 != 0 ||
         rowb / 8 > 256)
         return 0;
     for (int rb = dy; rb >= 2; --rb)

@@ -389,12 +389,14 @@ __device__ __forceinline__ void forward_unit(const InstDesc& d, long long ul, un
 // pitch = the strip's bytes, every row on a 16-byte boundary), and each block
 // leaves as one tensor store at (strip start, first row, plane); rows and
 // columns past the volume's end are clipped by the copy.  Halo lanes (lane >=
-// gcells) stage into the warp's spare slot after the ring.  Three channels.
-template <int DX, bool BF16>
+// gcells) stage into the warp's spare slot after the ring.  C = 3 channels
+// (the displacement field) or 1 (scalar interpolation).
+template <int DX, bool BF16, int C = 3>
 __device__ __forceinline__ void forward_unit_tma(const InstDesc& d, const void* tmap, long long ul,
                                                  unsigned char* stage, int blk_bytes, int rb, int lane, int& ring,
                                                  unsigned* err) {
-    constexpr int C = 3, ES = BF16 ? 2 : 4;
+    static_assert(C == 1 || C == 3, "one (scalar) or three (displacement) channels");
+    constexpr int ES = BF16 ? 2 : 4;
     constexpr bool PK = fwd_packed<DX, BF16>();
     constexpr int VW = BF16 ? 1 : tile_vec<DX>();
     const FwdUnit u = fwd_unit(d, ul);
@@ -406,17 +408,20 @@ __device__ __forceinline__ void forward_unit_tma(const InstDesc& d, const void* 
         for (int m = 0; m < 4; ++m) {
             float a = 0.f, b = 0.f, c = 0.f;
             if (col < d.nx) {
-                const long long e = phi_elem(d, u.kz + n, u.jy + m, col);
-                BSI_GUARD(e >= 0 && e + 3 <= 3LL * d.nx * d.ny * d.nz, kErrPhiRead, err) {
+                // C channels per control point: [nz][ny][nx][C]
+                const long long e = (((long long)(u.kz + n) * d.ny + (u.jy + m)) * d.nx + col) * C;
+                BSI_GUARD(e >= 0 && e + C <= (long long)C * d.nx * d.ny * d.nz, kErrPhiRead, err) {
                     const float* p = d.phi + e;
                     a = __ldg(p);
-                    b = __ldg(p + 1);
-                    c = __ldg(p + 2);
+                    if (C == 3) {
+                        b = __ldg(p + 1);
+                        c = __ldg(p + 2);
+                    }
                 }
             }
             ph[n][m][0] = a;
-            ph[n][m][1] = b;
-            ph[n][m][2] = c;
+            ph[n][m][C > 1 ? 1 : 0] = C > 1 ? b : a;
+            ph[n][m][C > 2 ? 2 : 0] = C > 2 ? c : a;
         }
 
     const int z0 = u.kz * d.dz, zn = imin(d.dz, d.Z - z0);

@@ -59,9 +59,10 @@ cudaError_t launch_adjoint_rational(const RatDesc& d, const float* grad, float* 
 cudaError_t rational_err_read_clear(unsigned* out, cudaStream_t s);
 
 // Forward of one volume on the tensor-store path (fwd_tma_rows gives rb > 0;
-// map: the field as a 3-D tensor of 8-byte elements, box (strip, rb, 1)).
-cudaError_t launch_forward_tma(const Batch<1>& b, bool bf16, const CUtensorMap& map, int rb, cudaStream_t s,
-                               LaunchInfo* info);
+// map: the output as a 3-D tensor of 8-byte elements, box (strip, rb, 1));
+// channels: 3 (displacement field) or 1 (scalar interpolation).
+cudaError_t launch_forward_tma(const Batch<1>& b, bool bf16, int channels, const CUtensorMap& map, int rb,
+                               cudaStream_t s, LaunchInfo* info);
 
 // Scalar (one-channel) interpolation: Eq. 1 with grid [nz][ny][nx], output [Z][Y][X].
 cudaError_t launch_forward_scalar(const Batch<1>& b, bool bf16, bool generic, cudaStream_t s, LaunchInfo* info);

@@ -60,6 +60,38 @@ def test_scalar_is_channel_of_the_field_bitwise(shape, spacing):
             assert torch.equal(s, field[..., c]), (dt, c)
 
 
+# One-channel volumes whose rows leave by tensor stores in blocks of rows (FP32 at
+# x-spacings <= 3, BF16 at even x-spacings with X % 8 == 0): block heights 3..8,
+# ragged tails in x, y and z.
+TENSOR_STORE = [
+    ((7, 30, 64), (2, 6, 2)),
+    ((9, 22, 120), (3, 4, 4)),
+    ((5, 18, 336), (2, 3, 6)),
+    ((4, 17, 464), (2, 8, 8)),
+]
+
+
+@pytest.mark.parametrize("shape,spacing", TENSOR_STORE, ids=[f"{s}-{d}" for s, d in TENSOR_STORE])
+def test_scalar_tensor_store_blocks(shape, spacing):
+    """Against the oracle (FP32), BF16 against round-to-nearest-even of FP32, and
+    each against the same channel of the 3-channel field, bit for bit."""
+    rng = np.random.default_rng(11 + sum(shape))
+    phi = rng.uniform(-3, 3, synth.grid_shape(shape, spacing) + (3,)).astype(np.float32)
+    phit = torch.from_numpy(phi).to(dev())
+    coeff = phit[..., 1].contiguous()
+    f32 = P.bsi_scalar_forward(coeff, shape, spacing)
+    b16 = P.bsi_scalar_forward(coeff, shape, spacing, out_dtype=torch.bfloat16)
+    torch.cuda.synchronize()
+    want = _oracle_scalar(phi[..., 1], shape, spacing)
+    err = float(np.max(np.abs(f32.double().cpu().numpy() - want)))
+    assert err <= FWD_TOL * float(np.max(np.abs(phi[..., 1]))), err
+    assert torch.equal(b16.cpu(), f32.cpu().to(torch.bfloat16))
+    for dt, got in ((torch.float32, f32), (torch.bfloat16, b16)):
+        field = P.bsi_field_forward(phit, shape, spacing, out_dtype=dt)
+        torch.cuda.synchronize()
+        assert torch.equal(got, field[..., 1]), dt
+
+
 def test_scalar_direct_stores_equal_the_staged_path():
     """At x-spacing 4 with rows on 16-byte boundaries each lane stores its tile
     as one 16-byte vector; an output 4 bytes off that boundary takes the staged
