@@ -96,9 +96,9 @@ bsi_status bsi_field_forward(const bsi_geom* g, const float* phi, void* field, b
 
 /* Workspace bytes bsi_field_adjoint needs for geometry g (0 for an empty
  * volume); no counterpart in the paper (its kernels have no adjoint): the
- * most any of its launch plans can use, since the tile-planes
- * per warp unit are chosen per call (from the device's SM count) unless the
- * tile-config table fixes them. */
+ * most any of its launch plans can use, since the tile-planes (and, on the
+ * tensor-copy path, tile-rows) per warp unit are chosen per call (from the
+ * device's SM count) unless the tile-config table fixes the tile-planes. */
 size_t bsi_adjoint_workspace_bytes(const bsi_geom* g);
 
 /* Adjoint BSI: the transpose of Eq. 1 applied to a voxel gradient,
@@ -113,7 +113,11 @@ size_t bsi_adjoint_workspace_bytes(const bsi_geom* g);
  * Two kernels: per-warp partial sums over tiles, then a fixed-order reduce.
  * A gradient with X % 4 == 0 at a 16-byte-aligned address and dx <= 8 is read
  * by TMA tensor copies (one per block of rows), any other by one bulk copy per
- * row; both add the same terms in the same order (bitwise equal results). */
+ * row.  With one tile-row per warp unit both add the same terms in the same
+ * order (bitwise equal results); on the tensor-copy path a single volume at
+ * y-spacing 4..6 takes units of two tile-rows, which sum in another order
+ * (equal to rounding).  The same call on the same input always gives the same
+ * bits. */
 bsi_status bsi_field_adjoint(const bsi_geom* g, const float* grad_field, float* grad_phi,
                              void* workspace, size_t workspace_bytes, bsi_stream_t stream);
 
