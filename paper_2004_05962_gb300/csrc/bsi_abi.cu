@@ -421,6 +421,21 @@ static cudaError_t encode_field_map(const InstDesc& d, bool bf16, int rb, CUtens
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// BF16 at odd x-spacings >= 5: rows leave by tensor stores when strips of 24
+// tiles (g dx a multiple of 8: rows on 16-byte boundaries) take the place of the
+// default 29, whose rows end off 16-byte boundaries (512 x 512 x 300 at spacing
+// 5: 0.153 -> 0.146 ms; at spacing 3 the idle lanes cost more: 512^3 0.414 ->
+// 0.429 ms, not taken).  Re-plans d's strips; true when it did.
+static bool bf16_odd_strips(InstDesc& d, bool bf16, bool generic) {
+    if (!bf16 || generic || !(d.dx & 1) || d.dx < 5 || d.gcells != kGroupCells || d.units <= 0 ||
+        fwd_tma_rows(d.X, d.dx, d.dy, kBf16OddStripTiles, true) <= 0)
+        return false;
+    d.gcells = kBf16OddStripTiles;
+    d.nxg = (int)cdiv(d.ncx, d.gcells);
+    d.units = (long long)d.ncz * d.ncy * d.nxg;
+    return true;
+}
+
 // Rows per block when a single-volume forward of c channels takes the
 // tensor-store path, else 0.
 static int forward_tma_rows(const InstDesc& d, bool bf16, bool generic, int c = 3) {
@@ -448,19 +463,7 @@ static cudaError_t run_group(const Group& g, Op op, bool bf16, float* part, long
         Batch<1> b;
         to_batch(g, b);
         if (op == Op::Forward) {
-            // BF16 at odd x-spacings >= 5: rows leave by tensor stores when strips of
-            // 24 tiles (g dx a multiple of 8: rows on 16-byte boundaries) take the place
-            // of the default 29, whose rows end off 16-byte boundaries (512 x 512 x 300
-            // at spacing 5: 0.153 -> 0.146 ms; at spacing 3 the idle lanes cost more:
-            // 512^3 0.414 -> 0.429 ms, not taken)
-            InstDesc& d0 = b.inst[0];
-            if (bf16 && !g.generic && (d0.dx & 1) && d0.dx >= 5 && d0.gcells == kGroupCells && d0.units > 0 &&
-                fwd_tma_rows(d0.X, d0.dx, d0.dy, kBf16OddStripTiles, true) > 0) {
-                d0.gcells = kBf16OddStripTiles;
-                d0.nxg = (int)cdiv(d0.ncx, d0.gcells);
-                d0.units = (long long)d0.ncz * d0.ncy * d0.nxg;
-                b.total_units = d0.units;
-            }
+            if (bf16_odd_strips(b.inst[0], bf16, g.generic)) b.total_units = b.inst[0].units;
             const int rb = forward_tma_rows(b.inst[0], bf16, g.generic);
             if (rb > 0) {
                 CUtensorMap map;
@@ -632,6 +635,35 @@ static void check_slots(long long total, RangeChecker& rc) {
 // the rows of the units tile the field exactly once.
 // ob: staging bytes per voxel (12 / 6 forward FP32 / BF16, 12 for T in both
 // resampling modes); outputs are checked as voxel ranges.
+// The tensor-store path of a single-volume forward (as run_group plans it for a
+// 16-byte-aligned field): every box starts on a 16-byte boundary at a
+// non-negative coordinate, is at most 256 elements wide, covers exactly its
+// strip (or runs past the volume's end, where the copy clips it), stays in its
+// tile-row, and every lane's staging stays in its block row or the spare slot.
+static void check_forward_tma(const InstDesc& d0, bool bf16, int c, RangeChecker& rc) {
+    InstDesc d = d0;
+    if (c == 3) bf16_odd_strips(d, bf16, false);
+    if (c == 1 && !bf16 && d.dx == 4) return;   // direct stores (bsi_scalar_forward)
+    const int rb = fwd_tma_rows(d.X, d.dx, d.dy, d.gcells, bf16, c);
+    if (rb <= 0) return;
+    const int es = bf16 ? 2 : 4, tile = d.dx * c * es;
+    const int rowb = fwd_tma_row_bytes(d.gcells, d.dx, bf16, c);
+    const int blk = pad128(rb * rowb), wsm = fwd_tma_warp_smem(blk);
+    if (rowb % 16 != 0 || rowb / 8 > 256) rc.fail("tensor-store box width", rowb, 256 * 8);
+    if (d.dy % rb != 0 || rb * rowb > blk) rc.fail("tensor-store block rows", rb, d.dy);
+    if (tile > 128) rc.fail("halo lane slot", tile, 128);
+    if ((long long)warps_per_cta(wsm, d.warps_req) * wsm + 128 > kSmemBudget)
+        rc.fail("tensor-store shared memory over budget", wsm, kSmemBudget);
+    if ((long long)c * d.X * es % 16 != 0) rc.fail("tensor-store row pitch", d.X, es);
+    for (long long ul = 0; ul < d.units; ++ul) {
+        const FwdUnit u = fwd_unit(d, ul);
+        const long long xb = (long long)u.x0 * c * es;
+        if (xb < 0 || xb % 16 != 0) rc.fail("tensor-store box start", u.x0, xb);
+        if (u.x0 + d.gcells * d.dx < d.X && u.nvox != d.gcells * d.dx) rc.fail("box past its strip", u.x0, u.nvox);
+        if (u.ncell > d.gcells || (long long)(u.ncell - 1) * tile + tile > rowb) rc.fail("lane past block row", u.ncell, rowb);
+    }
+}
+
 static void check_forward_group(const Group& g, int ob, RangeChecker& rc, bool cover) {
     const int buf = stage_buf_bytes(g.dxmax);
     for (const InstDesc& d : g.inst) {
@@ -1194,6 +1226,9 @@ int bsi_selfcheck_ranges(const bsi_instance* inst, int n, int op, int cover, cha
                 // staging bytes per voxel: the field (12 FP32, 6 BF16), T for both
                 // resampling modes (12), the scalar forward (4 FP32, 2 BF16)
                 check_forward_group(g, op == 1 ? 6 : op == 5 ? 4 : op == 6 ? 2 : 12, rc, cover != 0);
+                // the single-volume forward's tensor-store path (3 or 1 channels)
+                if ((op == 0 || op == 1 || op == 5 || op == 6) && n == 1 && g.inst.size() == 1 && !g.generic)
+                    check_forward_tma(g.inst[0], op == 1 || op == 6, op >= 5 ? 1 : 3, rc);
                 long long total = 0;
                 for (const InstDesc& d : g.inst) total += d.units;
                 if (cover) check_slots(total, rc);

@@ -156,6 +156,34 @@ def test_selfcheck_edge_cases(lib, op):
         assert n == 0, (shape, spacing, msg)
 
 
+# Single volumes whose forward rows leave by tensor stores in blocks (16-byte
+# rows and strips): FP32 at x-spacings <= 4, BF16 at even x-spacings and (24-tile
+# strips) odd ones >= 5, one and three channels, block heights 2..8, the CT and
+# 512^3 bench shapes.
+TENSOR_STORE = [
+    ((300, 512, 512), (5, 5, 5)),
+    ((512, 512, 512), (3, 3, 3)),
+    ((512, 512, 512), (4, 4, 4)),
+    ((512, 512, 512), (8, 8, 8)),
+    ((512, 512, 512), (6, 5, 4)),
+    ((7, 13, 64), (2, 3, 1)),
+    ((9, 22, 120), (3, 4, 2)),
+    ((10, 17, 252), (4, 6, 3)),
+    ((5, 30, 236), (2, 8, 4)),
+    ((6, 23, 248), (2, 5, 5)),
+    ((4, 17, 464), (2, 8, 8)),
+    ((7, 30, 64), (2, 6, 2)),
+    ((5, 18, 336), (2, 3, 6)),
+]
+
+
+@pytest.mark.parametrize("op", ["forward", "forward_bf16", "scalar", "scalar_bf16"])
+def test_selfcheck_tensor_store_blocks(lib, op):
+    for shape, spacing in TENSOR_STORE:
+        n, msg = P.bsi_selfcheck_ranges([shape], [spacing], op, cover=shape[0] * shape[1] * shape[2] < 1e8)
+        assert n == 0, (shape, spacing, msg)
+
+
 @pytest.mark.parametrize("op", ["forward", "adjoint", "resample", "resample_grad", "scalar", "scalar_bf16"])
 def test_selfcheck_random_geometries(lib, op):
     rng = np.random.default_rng(7)
