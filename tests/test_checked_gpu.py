@@ -12,8 +12,10 @@ from gpu_util import dev
 
 pytestmark = pytest.mark.gpu
 
+# 64^3 at 5: BF16 rows in tensor-store blocks (24-tile strips), adjoint units of
+# two tile-rows; (10, 17, 252) at (4, 6, 3): FP32 rows in blocks of 3 rows
 CASES = [((64, 64, 64), (5, 5, 5)), ((9, 8, 140), (3, 5, 13)), ((6, 7, 179), (2, 3, 2)),
-         ((5, 4, 130), (2, 2, 64)), ((1, 1, 1), (1, 1, 1))]
+         ((5, 4, 130), (2, 2, 64)), ((1, 1, 1), (1, 1, 1)), ((10, 17, 252), (4, 6, 3))]
 
 
 def _run(phi, shape, spacing, g):
