@@ -148,38 +148,55 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return w;
 }
 
-// Stores the N values (N even) of a lane's tile as BF16 (nearest even) from
-// shared byte address s (2-byte aligned), two values per 32-bit word, each
-// pair converted by one packed instruction; 8- or 16-byte stores where the
-// start allows.  A run starting 2 bytes past a word boundary stores its first
-// value alone and then the pairs shifted by one value (each word a byte
-// permute of two neighbouring converted pairs).  One 16-bit store per value,
-// at the lane stride of 6 DX bytes, meets up to 4-way bank conflicts
-// (x-spacing 8: 0.35 -> 0.19 ms for 512^3).  Odd N (odd x-spacings) keeps
-// the 16-bit stores: there neighbouring lanes alternate between the two
-// alignments, and the permuted form measured 1.5% slower.
+// Stores the N values of a lane's tile as BF16 (nearest even) from shared byte
+// address s (2-byte aligned), two values per 32-bit word, each pair converted
+// by one packed instruction; 8- or 16-byte stores where the start allows.  A
+// run starting 2 bytes past a word boundary stores its first value alone and
+// then the pairs shifted by one value (each word a byte permute of two
+// neighbouring converted pairs).  One 16-bit store per value, at the lane
+// stride of 6 DX bytes, meets up to 4-way bank conflicts (x-spacing 8: 0.35 ->
+// 0.19 ms for 512^3).  Odd N (odd x-spacings): neighbouring lanes alternate
+// between the two alignments, so each lane picks its permutation at run time;
+// on the per-row store path that measured 1.5% slower than 16-bit stores and
+// is not used there, on the tensor-store path 7% faster (512 x 512 x 300 at
+// spacing 5: 0.146 -> 0.136 ms).
 template <int N>
 __device__ __forceinline__ void sts_bf16_run(uint32_t s, const float (&v)[N]) {
-    static_assert(N % 2 == 0, "pairs of values");
-    uint32_t w[N / 2];
+    if constexpr (N % 2 == 0) {
+        uint32_t w[N / 2];
 #pragma unroll
-    for (int j = 0; j < N / 2; ++j) w[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
-    if ((s & 2u) == 0) {
-        if (N % 8 == 0 && (s & 15u) == 0) {
+        for (int j = 0; j < N / 2; ++j) w[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
+        // runs 2N bytes apart: every lane of the warp takes the same branch
+        if ((s & 2u) == 0) {
+            if (N % 8 == 0 && (s & 15u) == 0) {
 #pragma unroll
-            for (int j = 0; j < N / 2; j += 4) sts_v4_b32(s + 4 * j, w[j], w[j + 1], w[j + 2], w[j + 3]);
-        } else if (N % 4 == 0 && (s & 7u) == 0) {
+                for (int j = 0; j < N / 2; j += 4) sts_v4_b32(s + 4 * j, w[j], w[j + 1], w[j + 2], w[j + 3]);
+            } else if (N % 4 == 0 && (s & 7u) == 0) {
 #pragma unroll
-            for (int j = 0; j < N / 2; j += 2) sts_v2_b32(s + 4 * j, w[j], w[j + 1]);
+                for (int j = 0; j < N / 2; j += 2) sts_v2_b32(s + 4 * j, w[j], w[j + 1]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < N / 2; ++j) sts_b32(s + 4 * j, w[j]);
+            }
         } else {
+            sts_b16(s, (unsigned short)(w[0] & 0xffffu));
 #pragma unroll
-            for (int j = 0; j < N / 2; ++j) sts_b32(s + 4 * j, w[j]);
+            for (int j = 0; j + 1 < N / 2; ++j) sts_b32(s + 2 + 4 * j, __byte_perm(w[j], w[j + 1], 0x5432));
+            sts_b16(s + 2 * (N - 1), (unsigned short)(w[N / 2 - 1] >> 16));
         }
     } else {
-        sts_b16(s, (unsigned short)(w[0] & 0xffffu));
+        // (N + 1) / 2 pairs, the last one padded with a zero
+        uint32_t w[N / 2 + 1];
 #pragma unroll
-        for (int j = 0; j + 1 < N / 2; ++j) sts_b32(s + 2 + 4 * j, __byte_perm(w[j], w[j + 1], 0x5432));
-        sts_b16(s + 2 * (N - 1), (unsigned short)(w[N / 2 - 1] >> 16));
+        for (int j = 0; j < N / 2; ++j) w[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
+        w[N / 2] = pack_bf16x2(v[N - 1], 0.f);
+        // word-aligned start: pairs (0,1), (2,3), ... then the last value alone;
+        // 2 bytes past: the first value alone, then pairs (1,2), (3,4), ...
+        const uint32_t odd = (s >> 1) & 1u;
+        const uint32_t sel = odd ? 0x5432u : 0x3210u;
+#pragma unroll
+        for (int j = 0; j < N / 2; ++j) sts_b32(s + 2 * odd + 4 * j, __byte_perm(w[j], w[j + 1], sel));
+        sts_b16(odd ? s : s + 2 * (N - 1), (unsigned short)((odd ? w[0] : w[N / 2]) & 0xffffu));
     }
 }
 
@@ -207,11 +224,12 @@ __host__ __device__ constexpr int tile_vec() {
 
 // x-stage of a whole tile of DX voxels staged from shared address sv: FP32
 // with VW-float stores (sv aligned to 4 VW bytes), BF16 through sts_bf16_run
-// when the tile holds an even number of values, else one value at a time.
-template <int DX, int VW, bool BF16, int C, bool PK = fwd_packed<DX, BF16>()>
+// when the tile holds an even number of values or ODD_WORDS is set (the
+// tensor-store path), else one value at a time.
+template <int DX, int VW, bool BF16, int C, bool PK = fwd_packed<DX, BF16>(), bool ODD_WORDS = false>
 __device__ __forceinline__ void emit_tile(uint32_t sv, const float (&p0)[C], const float (&p1)[C],
                                           const float (&p2)[C], const float (&p3)[C]) {
-    constexpr bool kWords = BF16 && (C * DX) % 2 == 0;
+    constexpr bool kWords = BF16 && ((C * DX) % 2 == 0 || ODD_WORDS);
     if (!kWords && VW == 1) {
 #pragma unroll
         for (int r = 0; r < DX; ++r)
@@ -461,7 +479,7 @@ __device__ __forceinline__ void forward_unit_tma(const InstDesc& d, const void* 
                 }
                 // halo lanes write the spare slot again for every row (never copied out)
                 const uint32_t sv = sv0 + (lane < d.gcells ? (uint32_t)(r * rowb) : 0u);
-                emit_tile<DX, VW, BF16, C, PK>(sv, p0, p1, p2, p3);
+                emit_tile<DX, VW, BF16, C, PK, true>(sv, p0, p1, p2, p3);
             }
             fence_proxy_async_smem();  // this lane's staging writes before the tensor store reads them
             __syncwarp();
