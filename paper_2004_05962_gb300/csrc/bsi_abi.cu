@@ -1236,6 +1236,17 @@ int bsi_selfcheck_ranges(const bsi_instance* inst, int n, int op, int cover, cha
         } else {
             long long ws = 0;
             const std::vector<Group> groups = plan(descs(inst, n, true, false, true), &ws, true);
+            // the documented workspace (the bound over every plan) holds the planned one
+            long long bound = 0;
+            for (int i = 0; i < n; ++i) bound += adj_floats_bound(inst[i].geom);
+            if (ws > bound) rc.fail("planned workspace over the documented bound", ws, bound);
+            // and so does the least bound the no-alloc entry point admits a volume by
+            if (n == 1) {
+                long long ws1 = 0;
+                const long long least = adj_floats_bound(inst[0].geom, true);
+                (void)plan(descs(inst, 1, true, false, true, least), &ws1, true);
+                if (ws1 > least) rc.fail("no plan fits the least bound", ws1, least);
+            }
             for (const Group& g : groups) {
                 check_adjoint_group(g, ws, rc, cover != 0);
                 long long total = 0;

@@ -184,6 +184,20 @@ def test_selfcheck_tensor_store_blocks(lib, op):
         assert n == 0, (shape, spacing, msg)
 
 
+def test_selfcheck_two_row_adjoint_units(lib):
+    """Single volumes at y-spacings 4..6 plan units of two tile-rows on the
+    tensor-copy path: every partial write and read in range, every read written
+    first, and the plan inside the documented (and the no-alloc) workspace bound."""
+    cases = [((40, 18, 48), (3, 5, 4)), ((8, 40, 64), (2, 6, 4)), ((13, 24, 100), (5, 4, 3)),
+             ((11, 13, 40), (3, 5, 2)), ((20, 21, 4), (5, 5, 5)), ((7, 9, 96), (2, 4, 8))]
+    for shape, spacing in cases:
+        n, msg = P.bsi_selfcheck_ranges([shape], [spacing], "adjoint", cover=True)
+        assert n == 0, (shape, spacing, msg)
+    for shape, spacing in [((300, 512, 512), (5, 5, 5)), ((512, 512, 512), (6, 5, 4))]:
+        n, msg = P.bsi_selfcheck_ranges([shape], [spacing], "adjoint", cover=False)
+        assert n == 0, (shape, spacing, msg)
+
+
 @pytest.mark.parametrize("op", ["forward", "adjoint", "resample", "resample_grad", "scalar", "scalar_bf16"])
 def test_selfcheck_random_geometries(lib, op):
     rng = np.random.default_rng(7)
